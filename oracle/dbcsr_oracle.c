@@ -1,0 +1,421 @@
+/*
+ * dbcsr_oracle.c -- TEST INFRASTRUCTURE, NOT PART OF THE PRODUCT.
+ *
+ * A plain, slow, obviously correct CPU statement of what the GPU library
+ * computes, written from the paper (Sivkov, Lazzaro, Hutter: "DBCSR: A Library
+ * for Dense Matrix Multiplications on Distributed GPU-Accelerated Systems").
+ * Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may load
+ * it. It shares no code, header or table with the CUDA library.
+ *
+ * What it states:
+ *   - the local block-sparse product C = alpha*op(A)*op(B) + beta*C on the
+ *     blocked-CSR layout: "pairwise multiplications of small dense matrix
+ *     blocks, (m x k) for A blocks and (k x n) for B blocks" (Sec. II);
+ *   - the stack list of Sec. II (Traversal / Generation: batches of at most
+ *     30'000 block multiplications), in one canonical order;
+ *   - a double-double (Dot2, Ogita-Rump-Oishi 2005) accumulation mode used as
+ *     the near-exact reference for the precision studies;
+ *   - the INT8-slice emulation of FP64 (Ozaki et al. 2012 scheme, integer form)
+ *     step by step, so the GPU's emulated path can be checked slice by slice.
+ *
+ * Arithmetic: IEEE FP64, compiled with -ffp-contract=off so every a*b+c is a
+ * rounded product followed by a rounded sum, in the order written.
+ * Intra-block storage is column-major (the library is Fortran, Sec. II).
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* One matrix as the tests hand it over: a block index in any order and the
+ * blocks' data concatenated in that same order, each block column-major. */
+typedef struct {
+    int nbr, nbc;              /* number of block rows / block columns        */
+    const int *rs, *cs;        /* block row sizes [nbr], block col sizes [nbc] */
+    int64_t nblks;             /* number of stored blocks                     */
+    const int *br, *bc;        /* block coordinates [nblks]                   */
+    const double *data;        /* sum over blocks of rs[br]*cs[bc] doubles    */
+} ob_mat;
+
+/* Internal row-wise view: for block row i, the stored blocks sorted by column,
+ * each with a pointer to its (already op()-applied) column-major data. */
+typedef struct {
+    int nbr, nbc;
+    int *rs, *cs;
+    int64_t *rowptr;           /* [nbr+1]                                     */
+    int *col;                  /* [nblks] column of each block, row-sorted    */
+    const double **blk;        /* [nblks] data pointer of each block          */
+    double *own;               /* storage for transposed blocks, or NULL      */
+} ob_rows;
+
+static int cmp_i64pair(const void *x, const void *y)
+{
+    const int64_t *a = (const int64_t *)x, *b = (const int64_t *)y;
+    if (a[0] != b[0]) return a[0] < b[0] ? -1 : 1;
+    if (a[1] != b[1]) return a[1] < b[1] ? -1 : 1;
+    return 0;
+}
+
+static void rows_free(ob_rows *v)
+{
+    free(v->rs); free(v->cs); free(v->rowptr); free(v->col);
+    free((void *)v->blk); free(v->own);
+    memset(v, 0, sizeof(*v));
+}
+
+/* Build the row view of op(M). For op = 'N' the block (i,k) of op(M) is the
+ * stored block (i,k). For op = 'T' (or 'C', identical for real data) the block
+ * (i,k) of op(M) is the transpose of the stored block (k,i): the block grid is
+ * transposed and the row/column size arrays swap roles. Transposed blocks are
+ * copied element by element into owned storage. Returns 0, or -1 on a
+ * duplicate block / allocation failure. */
+static int rows_build(const ob_mat *M, char op, ob_rows *v)
+{
+    int tr = (op == 'T' || op == 't' || op == 'C' || op == 'c');
+    memset(v, 0, sizeof(*v));
+    v->nbr = tr ? M->nbc : M->nbr;
+    v->nbc = tr ? M->nbr : M->nbc;
+    v->rs = (int *)malloc(sizeof(int) * (size_t)(v->nbr + 1));
+    v->cs = (int *)malloc(sizeof(int) * (size_t)(v->nbc + 1));
+    v->rowptr = (int64_t *)calloc((size_t)v->nbr + 1, sizeof(int64_t));
+    v->col = (int *)malloc(sizeof(int) * (size_t)(M->nblks + 1));
+    v->blk = (const double **)malloc(sizeof(double *) * (size_t)(M->nblks + 1));
+    int64_t *order = (int64_t *)malloc(sizeof(int64_t) * 3 * (size_t)(M->nblks + 1));
+    int64_t *off = (int64_t *)malloc(sizeof(int64_t) * (size_t)(M->nblks + 1));
+    if (!v->rs || !v->cs || !v->rowptr || !v->col || !v->blk || !order || !off) {
+        free(order); free(off); rows_free(v); return -1;
+    }
+    for (int i = 0; i < v->nbr; i++) v->rs[i] = tr ? M->cs[i] : M->rs[i];
+    for (int j = 0; j < v->nbc; j++) v->cs[j] = tr ? M->rs[j] : M->cs[j];
+
+    /* data offset of every stored block, in the order given */
+    int64_t total = 0;
+    for (int64_t b = 0; b < M->nblks; b++) {
+        off[b] = total;
+        total += (int64_t)M->rs[M->br[b]] * M->cs[M->bc[b]];
+    }
+    /* sort (row, col) of op(M) -- stored block b sits at (bc,br) if transposed */
+    for (int64_t b = 0; b < M->nblks; b++) {
+        int64_t r = tr ? M->bc[b] : M->br[b];
+        int64_t c = tr ? M->br[b] : M->bc[b];
+        order[3 * b + 0] = r * (int64_t)(v->nbc + 1) + c;
+        order[3 * b + 1] = b;
+        order[3 * b + 2] = 0;
+    }
+    qsort(order, (size_t)M->nblks, 3 * sizeof(int64_t), cmp_i64pair);
+    if (tr) {
+        v->own = (double *)malloc(sizeof(double) * (size_t)(total + 1));
+        if (!v->own) { free(order); free(off); rows_free(v); return -1; }
+    }
+    int64_t pos = 0;
+    for (int64_t q = 0; q < M->nblks; q++) {
+        int64_t b = order[3 * q + 1];
+        int r = (int)(order[3 * q + 0] / (v->nbc + 1));
+        int c = (int)(order[3 * q + 0] % (v->nbc + 1));
+        if (q > 0 && order[3 * q + 0] == order[3 * (q - 1) + 0]) {
+            free(order); free(off); rows_free(v); return -1;   /* duplicate */
+        }
+        v->rowptr[r + 1]++;
+        v->col[q] = c;
+        if (!tr) {
+            v->blk[q] = M->data + off[b];
+        } else {
+            /* stored block is (sr x sc) = (cs_op[c] x rs_op[r]); op block is its transpose */
+            int sr = M->rs[M->br[b]], sc = M->cs[M->bc[b]];
+            const double *src = M->data + off[b];
+            double *dst = v->own + pos;
+            for (int x = 0; x < sc; x++)          /* op row    x = stored col */
+                for (int y = 0; y < sr; y++)      /* op column y = stored row */
+                    dst[x + (int64_t)y * sc] = src[y + (int64_t)x * sr];
+            v->blk[q] = dst;
+            pos += (int64_t)sr * sc;
+        }
+    }
+    for (int i = 0; i < v->nbr; i++) v->rowptr[i + 1] += v->rowptr[i];
+    free(order); free(off);
+    return 0;
+}
+
+/* ---------------------------------------------------------------------------
+ * Local block-sparse product, Sec. II.
+ *
+ *   C_ij = alpha * sum_k op(A)_ik * op(B)_kj  +  beta * C_ij(old)
+ *
+ * The result pattern is the set of (i,j) reached by at least one product
+ * op(A)_ik op(B)_kj, united with the old C pattern when beta != 0. With
+ * beta == 0 the old C is never read (a NaN in it does not propagate).
+ * Every element sum runs over k ascending and, inside a block product, over
+ * the inner index l ascending: acc += a[r,l]*b[l,c], then
+ * C = (alpha*acc) + (beta*Cold). mode 1 carries the sum in double-double.
+ *
+ * Rows: rows_sel (ascending, distinct) restricts the computation to those
+ * block rows of C (NULL = all rows). Output in row order, columns ascending.
+ * Call first with out_br == NULL to get *out_nblks and *out_nelems.
+ * ------------------------------------------------------------------------- */
+
+/* Dot2 building blocks (Ogita, Rump, Oishi 2005): TwoSum (Knuth) and
+ * TwoProduct (via a fused multiply-add, which returns the exact error). */
+static inline void two_sum(double a, double b, double *s, double *e)
+{
+    double x = a + b;
+    double z = x - a;
+    *e = (a - (x - z)) + (b - z);
+    *s = x;
+}
+static inline void two_prod(double a, double b, double *p, double *e)
+{
+    double x = a * b;
+    *e = fma(a, b, -x);
+    *p = x;
+}
+
+typedef struct {
+    int64_t nblks, nelems;
+} row_count;
+
+/* pattern of C row i: mark[j] = 1 for every reached column; returns count */
+static void row_pattern(const ob_rows *a, const ob_rows *b, const ob_rows *cold,
+                        int use_old, int i, unsigned char *mark)
+{
+    memset(mark, 0, (size_t)b->nbc);
+    for (int64_t p = a->rowptr[i]; p < a->rowptr[i + 1]; p++) {
+        int k = a->col[p];
+        for (int64_t q = b->rowptr[k]; q < b->rowptr[k + 1]; q++) mark[b->col[q]] = 1;
+    }
+    if (use_old)
+        for (int64_t q = cold->rowptr[i]; q < cold->rowptr[i + 1]; q++) mark[cold->col[q]] = 1;
+}
+
+int oracle_multiply(char ta, char tb, double alpha, const ob_mat *A, const ob_mat *B,
+                    double beta, const ob_mat *C, const int *rows_sel, int nrows_sel,
+                    int mode, int nthreads,
+                    int64_t *out_nblks, int64_t *out_nelems,
+                    int *out_br, int *out_bc, int64_t *out_off, double *out_data)
+{
+    ob_rows a, b, c;
+    int use_old = (beta != 0.0) && C && C->nblks > 0;
+    if (rows_build(A, ta, &a)) return -1;
+    if (rows_build(B, tb, &b)) { rows_free(&a); return -1; }
+    memset(&c, 0, sizeof(c));
+    if (C && rows_build(C, 'N', &c)) { rows_free(&a); rows_free(&b); return -1; }
+    if (a.nbc != b.nbr) { rows_free(&a); rows_free(&b); rows_free(&c); return -2; }
+    for (int k = 0; k < a.nbc; k++)
+        if (a.cs[k] != b.rs[k]) { rows_free(&a); rows_free(&b); rows_free(&c); return -2; }
+    if (C && (c.nbr != a.nbr || c.nbc != b.nbc)) { rows_free(&a); rows_free(&b); rows_free(&c); return -2; }
+    if (C) {
+        for (int i = 0; i < a.nbr; i++) if (c.rs[i] != a.rs[i]) { rows_free(&a); rows_free(&b); rows_free(&c); return -2; }
+        for (int j = 0; j < b.nbc; j++) if (c.cs[j] != b.cs[j]) { rows_free(&a); rows_free(&b); rows_free(&c); return -2; }
+    }
+    int nsel = rows_sel ? nrows_sel : a.nbr;
+    row_count *cnt = (row_count *)calloc((size_t)nsel + 1, sizeof(row_count));
+    if (!cnt) { rows_free(&a); rows_free(&b); rows_free(&c); return -1; }
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+
+    /* phase 1: per row, the number of C blocks and elements */
+#pragma omp parallel
+    {
+        unsigned char *mark = (unsigned char *)malloc((size_t)b.nbc + 1);
+#pragma omp for schedule(dynamic, 1)
+        for (int s = 0; s < nsel; s++) {
+            int i = rows_sel ? rows_sel[s] : s;
+            row_pattern(&a, &b, &c, use_old, i, mark);
+            int64_t nb = 0, ne = 0;
+            for (int j = 0; j < b.nbc; j++)
+                if (mark[j]) { nb++; ne += (int64_t)a.rs[i] * b.cs[j]; }
+            cnt[s].nblks = nb; cnt[s].nelems = ne;
+        }
+        free(mark);
+    }
+    int64_t tb_ = 0, te_ = 0;
+    for (int s = 0; s < nsel; s++) { tb_ += cnt[s].nblks; te_ += cnt[s].nelems; }
+    *out_nblks = tb_; *out_nelems = te_;
+    if (!out_br) { free(cnt); rows_free(&a); rows_free(&b); rows_free(&c); return 0; }
+
+    /* row start positions (blocks, elements) */
+    int64_t *bstart = (int64_t *)malloc(sizeof(int64_t) * ((size_t)nsel + 1));
+    int64_t *estart = (int64_t *)malloc(sizeof(int64_t) * ((size_t)nsel + 1));
+    bstart[0] = 0; estart[0] = 0;
+    for (int s = 0; s < nsel; s++) {
+        bstart[s + 1] = bstart[s] + cnt[s].nblks;
+        estart[s + 1] = estart[s] + cnt[s].nelems;
+    }
+
+    /* phase 2: values */
+#pragma omp parallel
+    {
+        unsigned char *mark = (unsigned char *)malloc((size_t)b.nbc + 1);
+        double **acc = (double **)calloc((size_t)b.nbc + 1, sizeof(double *));
+        double **cmp = (double **)calloc((size_t)b.nbc + 1, sizeof(double *));
+#pragma omp for schedule(dynamic, 1)
+        for (int s = 0; s < nsel; s++) {
+            int i = rows_sel ? rows_sel[s] : s;
+            int m = a.rs[i];
+            row_pattern(&a, &b, &c, use_old, i, mark);
+            /* place the row's blocks and zero their accumulators */
+            int64_t bp = bstart[s], ep = estart[s];
+            for (int j = 0; j < b.nbc; j++) {
+                if (!mark[j]) continue;
+                out_br[bp] = i; out_bc[bp] = j; out_off[bp] = ep;
+                acc[j] = out_data + ep;
+                size_t ne = (size_t)m * (size_t)b.cs[j];
+                memset(acc[j], 0, ne * sizeof(double));
+                if (mode == 1) cmp[j] = (double *)calloc(ne + 1, sizeof(double));
+                bp++; ep += (int64_t)ne;
+            }
+            /* k ascending over op(A)'s row i, then op(B)'s row k */
+            for (int64_t p = a.rowptr[i]; p < a.rowptr[i + 1]; p++) {
+                int k = a.col[p], kk = a.cs[k];
+                const double *ablk = a.blk[p];               /* m x kk */
+                for (int64_t q = b.rowptr[k]; q < b.rowptr[k + 1]; q++) {
+                    int j = b.col[q], n = b.cs[j];
+                    const double *bblk = b.blk[q];           /* kk x n */
+                    double *x = acc[j];
+                    for (int cc = 0; cc < n; cc++)
+                        for (int r = 0; r < m; r++) {
+                            if (mode == 1) {
+                                double sh = x[r + (int64_t)cc * m], sl = cmp[j][r + (int64_t)cc * m];
+                                for (int l = 0; l < kk; l++) {
+                                    double pr, pe, t, te;
+                                    two_prod(ablk[r + (int64_t)l * m], bblk[l + (int64_t)cc * kk], &pr, &pe);
+                                    two_sum(sh, pr, &t, &te);
+                                    sh = t;
+                                    sl = sl + (pe + te);
+                                }
+                                x[r + (int64_t)cc * m] = sh;
+                                cmp[j][r + (int64_t)cc * m] = sl;
+                            } else {
+                                double sum = x[r + (int64_t)cc * m];
+                                for (int l = 0; l < kk; l++)
+                                    sum = sum + ablk[r + (int64_t)l * m] * bblk[l + (int64_t)cc * kk];
+                                x[r + (int64_t)cc * m] = sum;
+                            }
+                        }
+                }
+            }
+            /* C = alpha*acc + beta*Cold */
+            int64_t q0 = use_old ? c.rowptr[i] : 0, q1 = use_old ? c.rowptr[i + 1] : 0;
+            for (int j = 0; j < b.nbc; j++) {
+                if (!mark[j]) continue;
+                size_t ne = (size_t)m * (size_t)b.cs[j];
+                const double *old = NULL;
+                for (int64_t q = q0; q < q1; q++) if (c.col[q] == j) { old = c.blk[q]; break; }
+                for (size_t e = 0; e < ne; e++) {
+                    double v = (mode == 1) ? acc[j][e] + cmp[j][e] : acc[j][e];
+                    double r = alpha * v;
+                    if (old) r = r + beta * old[e];
+                    acc[j][e] = r;
+                }
+                if (mode == 1) { free(cmp[j]); cmp[j] = NULL; }
+            }
+        }
+        free(mark); free(acc); free(cmp);
+    }
+    free(bstart); free(estart); free(cnt);
+    rows_free(&a); rows_free(&b); rows_free(&c);
+    return 0;
+}
+
+/* ---------------------------------------------------------------------------
+ * Stack list, Sec. II (Traversal + Generation).
+ *
+ * One entry per block product op(A)_ik op(B)_kj with both blocks stored. The
+ * paper fixes only the content of a batch (at most 30'000 multiplications of
+ * one kind); the canonical order used for comparison is: shape (m,n,k)
+ * ascending, then i, then j, then k. A stack is a maximal run of entries of
+ * one shape, cut every stack_cap entries. Each entry is written as 7 ints:
+ * stack id, m, n, k, i, j, kblk. Returns the number of entries, or <0.
+ * ------------------------------------------------------------------------- */
+static int cmp_entry(const void *x, const void *y)
+{
+    const int *a = (const int *)x, *b = (const int *)y;
+    for (int f = 1; f < 7; f++)
+        if (a[f] != b[f]) return a[f] < b[f] ? -1 : 1;
+    return 0;
+}
+
+int64_t oracle_stack_list(char ta, char tb, const ob_mat *A, const ob_mat *B,
+                          int stack_cap, int *out, int64_t cap)
+{
+    ob_rows a, b;
+    if (rows_build(A, ta, &a)) return -1;
+    if (rows_build(B, tb, &b)) { rows_free(&a); return -1; }
+    if (a.nbc != b.nbr) { rows_free(&a); rows_free(&b); return -2; }
+    int64_t n = 0;
+    for (int i = 0; i < a.nbr; i++)
+        for (int64_t p = a.rowptr[i]; p < a.rowptr[i + 1]; p++) {
+            int k = a.col[p];
+            n += b.rowptr[k + 1] - b.rowptr[k];
+        }
+    if (!out) { rows_free(&a); rows_free(&b); return n; }
+    if (n > cap) { rows_free(&a); rows_free(&b); return -3; }
+    int64_t e = 0;
+    for (int i = 0; i < a.nbr; i++)
+        for (int64_t p = a.rowptr[i]; p < a.rowptr[i + 1]; p++) {
+            int k = a.col[p];
+            for (int64_t q = b.rowptr[k]; q < b.rowptr[k + 1]; q++) {
+                int j = b.col[q];
+                int *x = out + 7 * e;
+                x[0] = 0; x[1] = a.rs[i]; x[2] = b.cs[j]; x[3] = a.cs[k];
+                x[4] = i; x[5] = j; x[6] = k;
+                e++;
+            }
+        }
+    qsort(out, (size_t)n, 7 * sizeof(int), cmp_entry);
+    int sid = -1, run = 0;
+    for (int64_t q = 0; q < n; q++) {
+        int *x = out + 7 * q;
+        int newshape = (q == 0) || x[1] != x[1 - 7] || x[2] != x[2 - 7] || x[3] != x[3 - 7];
+        if (newshape || run == stack_cap) { sid++; run = 0; }
+        x[0] = sid; run++;
+    }
+    rows_free(&a); rows_free(&b);
+    return n;
+}
+
+/* ---------------------------------------------------------------------------
+ * Dense column-major GEMM, plain triple loop: C = alpha*op(A)*op(B) + beta*C
+ * with op(A) M x K and op(B) K x N, summing l ascending. Used to state the
+ * densified product of Sec. III (one large block, batch size 1).
+ * lda/ldb/ldc are the column strides of the stored arrays.
+ * ------------------------------------------------------------------------- */
+void oracle_dense_gemm(char ta, char tb, int64_t M, int64_t N, int64_t K, double alpha,
+                       const double *A, int64_t lda, const double *B, int64_t ldb,
+                       double beta, double *C, int64_t ldc, int nthreads)
+{
+    int trA = (ta == 'T' || ta == 't' || ta == 'C' || ta == 'c');
+    int trB = (tb == 'T' || tb == 't' || tb == 'C' || tb == 'c');
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t c = 0; c < N; c++)
+        for (int64_t r = 0; r < M; r++) {
+            double s = 0.0;
+            for (int64_t l = 0; l < K; l++) {
+                double x = trA ? A[l + r * lda] : A[r + l * lda];
+                double y = trB ? B[c + l * ldb] : B[l + c * ldb];
+                s = s + x * y;
+            }
+            double v = alpha * s;
+            if (beta != 0.0) v = v + beta * C[r + c * ldc];
+            C[r + c * ldc] = v;
+        }
+}
+
+int oracle_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
