@@ -1,0 +1,391 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 local block-sparse multiply C = alpha*op(A)*op(B) + beta*C.
+
+Metric: useful FP64 TFLOP/s -- sum over the block products the multiply needs
+of 2*m*n*k, divided by the time of one whole dbcsr_multiply (stack
+generation or densification, the product kernels, undensification), inputs
+resident in HBM. Densified zeros and emulation slice work are not counted.
+
+Default workload: the dense limit, N = 11'264 as a 512 x 512 grid of 22 x 22
+blocks at 100% occupancy, entries U[-1,1], C = A*B + C (beta = 1). It is the
+paper's "square matrix" experiment with its block size 22 (Sec. IV), scaled
+to one GPU. Every input is larger than L2 (1 GB each, L2 is 129 MB), so no
+flush is needed between steps.
+
+One JSON line on stdout (rank 0). ``--impl reference`` times the CPU oracle
+(the plain FP64 block-triple loop) on a bounded sample of the same workload.
+Multi-GPU: replicas only (the single-GPU product does not shard here); each
+rank runs its own replica, value = all ranks' useful flops / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+# nominal dense rates (TFLOP/s) used to scale the measured bf16 peak to other dtypes
+NOMINAL = {"bf16": 2250.0, "tf32": 1100.0, "fp64": 1.25}
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return dict(FALLBACK), "fallback"
+
+
+def workload(name, scale):
+    from paper_1910_04796_gb300 import synth
+    if name == "dense-limit":
+        nblk = max(2, int(round(512 * scale)))
+        return synth.workload_dense_limit(seed=1, nblk=nblk, bs=22)
+    if name == "small-sparse":
+        return synth.workload_small_sparse(0)
+    if name == "uneven":
+        nblk = max(10, int(round(4000 * scale)))
+        return synth.workload_uneven(seed=3, nblk=nblk, width=max(1, int(400 * scale)))
+    if name == "precision-dense":
+        n = max(64, int(round(16384 * scale / 32)) * 32)
+        return synth.workload_precision_dense(seed=4, n=n)
+    if name == "precision-sparse":
+        nblk = max(8, int(round(1024 * scale)))
+        return synth.workload_precision_sparse(seed=5, nblk=nblk)
+    if name.startswith("tall-skinny"):
+        v = name.split("-")[-1]
+        mn = max(64, int(round(4096 * scale / 32)) * 32)
+        kk = max(64, int(round(131072 * scale / 32)) * 32)
+        return synth.workload_tall_skinny(seed=2, variant=v, mn=mn, kk=kk)
+    raise SystemExit(f"unknown workload {name}")
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if args.impl != "reference" else "gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_oracle_sample(w, rows, threads=0):
+    """Time the CPU oracle on the given C block rows of the workload."""
+    from oracle import oracle as O
+    t0 = time.perf_counter()
+    O.multiply(w.transa, w.transb, w.alpha, w.A, w.B, w.beta, w.C, rows=rows, nthreads=threads)
+    dt = time.perf_counter() - t0
+    # useful flops of the sampled rows: sum over products in those rows of 2*m*n*k
+    A, B = w.A, w.B
+    ta, tb = w.transa in "TC", w.transb in "TC"
+    a_r = A.blk_col if ta else A.blk_row
+    a_k = A.blk_row if ta else A.blk_col
+    a_m = (A.col_sizes if ta else A.row_sizes)
+    kk = (A.row_sizes if ta else A.col_sizes)
+    b_k = B.blk_col if tb else B.blk_row
+    b_j = B.blk_row if tb else B.blk_col
+    b_n = (B.row_sizes if tb else B.col_sizes)
+    nk = len(kk)
+    bn_sum = np.zeros(nk)
+    np.add.at(bn_sum, b_k, b_n[b_j].astype(np.float64))
+    sel = np.isin(a_r, np.asarray(rows))
+    fl = float((2.0 * a_m[a_r[sel]] * kk[a_k[sel]] * bn_sum[a_k[sel]]).sum())
+    return fl, dt
+
+
+def run_reference(args, world, rank):
+    """Reference arm: the CPU oracle as it stands, on a bounded sample of the workload."""
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    w = workload(args.workload, args.scale)
+    nrows = len(w.A.col_sizes if w.transa in "TC" else w.A.row_sizes)
+    threads = O.threads()
+    rows = list(range(0, nrows, max(1, nrows // max(1, args.ref_rows))))[:args.ref_rows]
+    vals = []
+    for _ in range(args.warmup if args.warmup < 2 else 1):
+        cpu_oracle_sample(w, rows[:1], threads)
+    flops_tot, t_tot = 0.0, 0.0
+    for _ in range(args.steps):
+        fl, dt = cpu_oracle_sample(w, rows, threads)
+        flops_tot += fl
+        t_tot += dt
+        vals.append(fl / dt / 1e12)
+    value = flops_tot / t_tot / 1e12
+    sample = f"{len(rows)} of {nrows} C block rows per step (oracle, OpenMP over C block rows)"
+    line = {
+        "impl": "reference", "metric": "useful FP64 TFLOP/s, block-sparse C+=A*B", "value": value,
+        "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * t_tot / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def time_steps(fn, steps, warmup, world):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    barrier(world)
+    wall = time.perf_counter() - t0
+    return e0.elapsed_time(e1) / 1000.0, wall
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="dense-limit")
+    ap.add_argument("--scale", type=float, default=1.0)
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "ozaki", "tf32"])
+    ap.add_argument("--path", default="auto", choices=["auto", "stacks", "dense"])
+    ap.add_argument("--slices", type=int, default=0)
+    ap.add_argument("--ref-rows", type=int, default=48, help="C block rows per oracle sample")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-legs", action="store_true", help="skip the plain-FP64 comparison legs")
+    args = ap.parse_args()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        return run_reference(args, world, rank)
+
+    import torch
+    from paper_1910_04796_gb300 import dbcsr
+
+    torch.cuda.set_device(local)
+    dbcsr.init()
+    pk, pk_kind = peaks()
+    w = workload(args.workload, args.scale)
+    precision = args.precision
+    if precision == "auto":
+        precision = "ozaki" if dbcsr.has_precision("ozaki") else "fp64"
+    rs = w.A.col_sizes if w.transa in "TC" else w.A.row_sizes
+    cs = w.B.row_sizes if w.transb in "TC" else w.B.col_sizes
+
+    # resident inputs (device data, created once)
+    A = dbcsr.Matrix.from_blocks(w.A)
+    B = dbcsr.Matrix.from_blocks(w.B)
+    C0 = w.C
+    if C0 is not None:
+        Cm = dbcsr.Matrix.from_blocks(C0)
+    else:
+        Cm = dbcsr.Matrix.create(rs, cs, np.zeros(0, np.int32), np.zeros(0, np.int32))
+
+    def step(prec=precision, path=args.path, timing=False):
+        dbcsr.multiply(w.transa, w.transb, w.alpha, A, B, w.beta, Cm, path=path, precision=prec,
+                       ozaki_slices=args.slices, timing=timing)
+
+    step()
+    st = dbcsr.stats()
+    useful = st["useful_flops"]
+    with Clocks(local) as clk:
+        secs, wall = time_steps(step, args.steps, max(args.warmup, 3) - 1, world)
+    launches = dbcsr.stats()["kernel_launches"] * args.steps
+    secs = max_over_ranks(secs, world)
+    value = useful * world * args.steps / secs / 1e12
+    # live timing of the dominant kernel (CUDA events on the library stream)
+    mains, totals = [], []
+    for _ in range(max(1, min(3, args.steps))):
+        step(timing=True)
+        s2 = dbcsr.stats()
+        mains.append(s2["ms_main"])
+        totals.append(s2["ms_total"])
+    main_ms = statistics.median(mains)
+    s2 = dbcsr.stats()
+    path_taken = {dbcsr.PATH_DENSE: "dense", dbcsr.PATH_STACKS: "stacks"}[s2["path"]]
+    if precision == "fp64":
+        bound, unit = "tensor" if path_taken == "dense" else "alu", "TFLOP/s"
+        peak = pk["bf16_tflops"] * NOMINAL["fp64"] / NOMINAL["bf16"]
+        peak_note = f"FP64 = {pk_kind} bf16 burst x nominal FP64/bf16 (1.25/2250)"
+        achieved = s2["main_flops"] / (main_ms / 1e3) / 1e12
+    elif precision == "ozaki":
+        bound, unit = "tensor", "TFLOP/s"
+        peak = pk["bf16_tflops_sustained"] if main_ms > 1000 else pk["bf16_tflops"]
+        peak_note = f"bf16 {'sustained' if main_ms > 1000 else 'burst'} ({pk_kind})"
+        achieved = s2["main_flops"] / (main_ms / 1e3) / 1e12
+    else:
+        bound, unit = "tensor", "TFLOP/s"
+        peak = pk["bf16_tflops"] * NOMINAL["tf32"] / NOMINAL["bf16"]
+        peak_note = f"TF32 = {pk_kind} bf16 burst x nominal TF32/bf16 (1100/2250)"
+        achieved = s2["main_flops"] / (main_ms / 1e3) / 1e12
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
+                "traffic": None, "kernel_ms": main_ms, "algorithmic_flops": s2["main_flops"],
+                "peak_source": peak_note}
+
+    # plain FP64 comparison legs (same GPU, same inputs)
+    legs = {}
+    if not args.no_legs and rank == 0:
+        for name, prec, path in (("fp64_dense", "fp64", "dense"), ("fp64_stacks", "fp64", "stacks")):
+            if prec == precision and path == path_taken:
+                legs[name] = value / world
+                continue
+            try:
+                s_leg, _ = time_steps(lambda: step(prec, path), 1, 1, 1)
+                legs[name] = useful / s_leg / 1e12
+            except Exception as e:  # report, do not hide
+                legs[name] = f"error: {e}"
+
+    # end to end through the C ABI with host buffers (H2D of inputs and D2H of C inside)
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+        hA, hB = pin(w.A.data), pin(w.B.data)
+        hC = pin(C0.data) if C0 is not None else None
+        out = None
+
+        def e2e_step():
+            nonlocal out
+            Ah = dbcsr.Matrix.create(w.A.row_sizes, w.A.col_sizes, w.A.blk_row, w.A.blk_col, hA)
+            Bh = dbcsr.Matrix.create(w.B.row_sizes, w.B.col_sizes, w.B.blk_row, w.B.blk_col, hB)
+            if C0 is not None:
+                Ch = dbcsr.Matrix.create(C0.row_sizes, C0.col_sizes, C0.blk_row, C0.blk_col, hC)
+            else:
+                Ch = dbcsr.Matrix.create(rs, cs, np.zeros(0, np.int32), np.zeros(0, np.int32))
+            dbcsr.multiply(w.transa, w.transb, w.alpha, Ah, Bh, w.beta, Ch, path=args.path, precision=precision,
+                           ozaki_slices=args.slices)
+            out = Ch.data()
+            for m in (Ah, Bh, Ch):
+                m.release()
+
+        e2e_steps = max(1, min(args.steps, 3))
+        s_e2e, _ = time_steps(e2e_step, e2e_steps, 1, world)
+        s_e2e = max_over_ranks(s_e2e, world)
+        h2d = (hA.nbytes + hB.nbytes + (hC.nbytes if hC is not None else 0)
+               + 4 * 2 * (w.A.nblks + w.B.nblks + (C0.nblks if C0 is not None else 0)))
+        e2e = {"value": useful * world * e2e_steps / s_e2e / 1e12, "unit": "TFLOP/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(out.nbytes if out is not None else 0)}
+
+    cpu = None
+    if not args.no_cpu and rank == 0 and world == 1:
+        from oracle import oracle as O
+        nrows = len(rs)
+        nsel = min(args.ref_rows, nrows)
+        rows = list(range(0, nrows, max(1, nrows // nsel)))[:nsel]
+        fl, dt = cpu_oracle_sample(w, rows, O.threads())
+        cpu = {"value": fl / dt / 1e12, "unit": "TFLOP/s", "cores": O.threads(), "kind": "oracle",
+               "sample": f"{len(rows)} of {nrows} C block rows ({dt:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": "useful FP64 TFLOP/s, block-sparse C+=A*B", "value": value, "unit": "TFLOP/s",
+            "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
+            "ms_per_step": 1000.0 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if precision == "fp64" else
+            ("f64 (emulated: int8-valued slices on bf16 tensor cores)" if precision == "ozaki" else "tf32"),
+            "data": "synthetic",
+            "config": {"workload": w.name, "path": path_taken, "precision": precision,
+                       "useful_flops_per_step": useful, "n_products": st["n_products"],
+                       "l2": "inputs larger than L2 (no flush)" if useful > 1e9 else "inputs in L2",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "clocks": clk.summary(), "legs_tflops": legs, "wall_s": wall,
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,212 @@
+/*
+ * dbcsr_gb.h -- C ABI of the GB300 (sm_103a) local block-sparse matrix product.
+ *
+ * The library computes, on one GPU,
+ *
+ *     C = alpha * op(A) * op(B) + beta * C,      op(X) in {X, X^T}
+ *
+ * for matrices stored in the blocked compressed sparse row layout that the
+ * paper describes (Sivkov, Lazzaro, Hutter, "DBCSR: A Library for Dense Matrix
+ * Multiplications on Distributed GPU-Accelerated Systems", Sec. II: "DBCSR
+ * matrices are stored in a blocked compressed sparse row (CSR) format"; the
+ * paper states that a C API is provided). Every stored block is a dense
+ * sub-matrix, column-major (the library the paper describes is Fortran), of
+ * size row_blk_sizes[i] x col_blk_sizes[j].
+ *
+ * The product is the paper's local multiplication (Sec. II): pairwise block
+ * products A_ik * B_kj, organised in stacks of block products grouped by block
+ * shape (m, n, k) and executed by batched small-matrix kernels; or, when both
+ * operands are dense, the densified path of Sec. III (all blocks coalesced into
+ * one large block, one GEMM, then the result split back into the original
+ * block sizes).
+ *
+ * Conventions for every entry point:
+ *   - Return value: DBCSR_OK (0) or a negative DBCSR_ERR_* code. The message of
+ *     the last error on the calling thread is available from dbcsr_last_error().
+ *     No C++ exception ever crosses this interface.
+ *   - All GPU work is ordered on the stream given to dbcsr_init() (default: the
+ *     legacy default stream). Entry points that return host data synchronise
+ *     that stream before returning.
+ *   - Device memory is obtained through the allocator set with
+ *     dbcsr_set_allocator(), else from CUDA's stream-ordered pool
+ *     (cudaMallocAsync on the library stream; freed blocks stay in the pool).
+ *   - Matrices are opaque handles owned by the library; dbcsr_release() frees
+ *     them. A handle may be used by one host thread at a time.
+ *   - Sizes and counts are int64_t where they can exceed 2^31; block counts of
+ *     one matrix must stay below 2^31 (DBCSR_ERR_OVERFLOW otherwise).
+ */
+#ifndef DBCSR_GB_H
+#define DBCSR_GB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define DBCSR_API __attribute__((visibility("default")))
+#else
+#define DBCSR_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DBCSR_OK            0
+#define DBCSR_ERR_ARG      -1  /* invalid argument (NULL handle, bad trans char, bad index) */
+#define DBCSR_ERR_DIM      -2  /* block grids or block sizes of A, B, C do not conform */
+#define DBCSR_ERR_ALLOC    -3  /* the device allocator returned NULL */
+#define DBCSR_ERR_OVERFLOW -4  /* a count exceeds what the index types can hold */
+#define DBCSR_ERR_TIMEOUT  -5  /* a bounded device-side wait gave up */
+#define DBCSR_ERR_CUDA     -6  /* a CUDA runtime call failed */
+#define DBCSR_ERR_STATE    -7  /* library not initialised / no device */
+
+typedef struct dbcsr_matrix_s *dbcsr_matrix;
+
+/* Device allocator hooks. alloc returns device memory of `bytes` usable in
+ * stream order on `stream` (a cudaStream_t), or NULL on failure. free releases
+ * a pointer returned by alloc; `bytes` is the size that was requested. */
+typedef void *(*dbcsr_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*dbcsr_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
+
+/* Execution path of dbcsr_multiply (Sec. II stacks vs Sec. III densification). */
+#define DBCSR_PATH_AUTO   0  /* dense path when op(A) and op(B) are 100% occupied, else stacks */
+#define DBCSR_PATH_STACKS 1  /* stacks of block products, batched small-GEMM kernels */
+#define DBCSR_PATH_DENSE  2  /* densify, one GEMM, undensify (any occupancy; absent blocks = 0) */
+
+/* Arithmetic of the multiply. */
+#define DBCSR_PREC_FP64  0   /* IEEE FP64 products and sums (DFMA / DMMA) */
+#define DBCSR_PREC_OZAKI 1   /* FP64 emulated with 7-bit integer slices on the tensor cores,
+                                exact integer accumulation, FP64 recombination */
+#define DBCSR_PREC_TF32  2   /* inputs rounded to TF32, FP32 accumulation (error reported only) */
+
+typedef struct {
+    int path;          /* DBCSR_PATH_*                                        */
+    int precision;     /* DBCSR_PREC_*                                        */
+    int ozaki_slices;  /* slices per operand for DBCSR_PREC_OZAKI; 0 = default (7) */
+    int kernel;        /* stack-kernel choice: 0 = autotuned table, 1 = generic */
+    int timing;        /* nonzero: time the phases with CUDA events on the
+                          library stream (reported by dbcsr_get_stats)        */
+    int reserved[3];   /* must be zero                                        */
+} dbcsr_opts;
+
+/* Statistics of the last dbcsr_multiply on the calling thread. */
+typedef struct {
+    int64_t n_products;      /* block products (stack entries)                   */
+    int64_t n_stacks;        /* stacks of <= 30000 entries per (m,n,k) shape      */
+    int64_t n_shapes;        /* distinct (m,n,k) shapes                           */
+    int64_t c_blocks;        /* blocks in the result C                            */
+    double useful_flops;     /* sum over block products of 2*m*n*k                */
+    int path;                /* path taken (DBCSR_PATH_STACKS or _DENSE)          */
+    int precision;           /* precision used                                    */
+    int kernel_launches;     /* kernels this library launched during the call     */
+    int reserved;
+    /* with dbcsr_opts.timing: milliseconds per phase, CUDA events on the stream */
+    float ms_setup;          /* stack generation, or densification of A, B, C    */
+    float ms_main;           /* the product kernels (batched small GEMM / GEMM)   */
+    float ms_finish;         /* undensification / index hand-over                 */
+    float ms_total;          /* whole call                                        */
+    double main_flops;       /* arithmetic the main kernels executed (2*M*N*K per
+                                GEMM issued, incl. slices / padding)             */
+    double main_bytes;       /* algorithmic HBM bytes of the main kernels         */
+} dbcsr_stats;
+
+/* Select the stream (a cudaStream_t, may be NULL for the legacy default
+ * stream) on which all following work is ordered, and the current CUDA
+ * device. Call once before anything else; may be called again to switch. */
+DBCSR_API int dbcsr_init(void *cuda_stream);
+
+/* Route device allocations through the given hooks (NULL, NULL restores the
+ * built-in stream-ordered pool). Every allocation is later returned to the
+ * hook (or pool) that made it, so the hooks may be switched at any time; the
+ * hook's ctx must stay valid while memory it allocated is alive. */
+DBCSR_API int dbcsr_set_allocator(dbcsr_alloc_fn alloc, dbcsr_free_fn free_fn, void *ctx);
+
+/* Create a matrix (Sec. II: a blocked CSR matrix with per-row and per-column
+ * block sizes).
+ *   nblkrows, nblkcols  : block grid (>= 0)
+ *   row_blk_sizes       : host int32[nblkrows], each >= 1
+ *   col_blk_sizes       : host int32[nblkcols], each >= 1
+ *   nblks               : number of stored blocks (>= 0)
+ *   blk_row, blk_col    : host int32[nblks], block coordinates in any order,
+ *                         no duplicates (DBCSR_ERR_ARG on a duplicate or an
+ *                         out-of-range coordinate)
+ *   data                : the blocks' values concatenated in the order of
+ *                         blk_row/blk_col, each block column-major; host
+ *                         memory if data_on_device == 0, device memory
+ *                         otherwise; NULL creates all-zero blocks
+ * The library copies everything; the caller keeps ownership of its arrays.
+ * Blocks are stored in CSR order (row, then column ascending). */
+DBCSR_API int dbcsr_create(dbcsr_matrix *out, int nblkrows, int nblkcols,
+                 const int *row_blk_sizes, const int *col_blk_sizes,
+                 int64_t nblks, const int *blk_row, const int *blk_col,
+                 const double *data, int data_on_device);
+
+/* Free a matrix and set *m to NULL. NULL or *m == NULL is a no-op. */
+DBCSR_API int dbcsr_release(dbcsr_matrix *m);
+
+/* Block grid, number of stored blocks and of stored elements. Any output
+ * pointer may be NULL. */
+DBCSR_API int dbcsr_get_info(dbcsr_matrix m, int *nblkrows, int *nblkcols, int64_t *nblks,
+                   int64_t *nelems);
+
+/* Block index in storage (CSR) order, to host arrays of length nblks:
+ * block row, block column, element offset of the block in the data array.
+ * Any output pointer may be NULL. */
+DBCSR_API int dbcsr_get_index(dbcsr_matrix m, int *blk_row, int *blk_col, int64_t *blk_off);
+
+/* All stored values in storage order (nelems doubles) to `out`, which is host
+ * memory if out_on_device == 0 and device memory otherwise. */
+DBCSR_API int dbcsr_get_data(dbcsr_matrix m, double *out, int out_on_device);
+
+/* Device pointer of the stored values (valid until the next call that changes
+ * the matrix) -- for callers that keep data resident on the GPU. */
+DBCSR_API int dbcsr_data_ptr(dbcsr_matrix m, double **dev_ptr);
+
+/* Copy block (row, col) to host `out_colmajor` (row_blk_size x col_blk_size
+ * doubles, column-major). *found = 1 if the block is stored, else 0 and `out`
+ * is left untouched. DBCSR_ERR_ARG for coordinates outside the grid. */
+DBCSR_API int dbcsr_get_block(dbcsr_matrix m, int row, int col, double *out_colmajor, int *found);
+
+/* C = alpha * op(A) * op(B) + beta * C (Sec. II local multiplication; Sec. III
+ * densification when the dense path is taken).
+ *   transa, transb : 'N' (op = identity), 'T' or 'C' (op = transpose; for real
+ *                    data 'C' equals 'T')
+ *   A, B, C        : existing matrices; C must have block rows = those of
+ *                    op(A), block columns = those of op(B), and the inner
+ *                    block sizes of op(A) and op(B) must agree one by one
+ *                    (DBCSR_ERR_DIM otherwise). C must differ from A and B.
+ *   opts           : NULL = DBCSR_PATH_AUTO, DBCSR_PREC_FP64.
+ * The result pattern is the set of (i,j) reached by at least one block
+ * product, united with C's old pattern when beta != 0. With beta == 0 the old
+ * C values are never read (NaN in them does not propagate). Blocks whose
+ * value cancels to zero stay stored. C's index and data are replaced. */
+DBCSR_API int dbcsr_multiply(char transa, char transb, double alpha, dbcsr_matrix A, dbcsr_matrix B,
+                   double beta, dbcsr_matrix C, const dbcsr_opts *opts);
+
+/* Statistics of the last dbcsr_multiply of this thread. */
+DBCSR_API int dbcsr_get_stats(dbcsr_stats *out);
+
+/* The stack list of Sec. II (Traversal + Generation), as the GPU builds it
+ * for op(A) * op(B): one entry per block product, 7 int32 each:
+ *   stack id, m, n, k, block row i, block column j, inner block index k.
+ * Canonical order: shape (m, n, k) ascending, then i, j, k ascending. A stack
+ * is a run of one shape, cut every `stack_cap` entries (the paper's batches
+ * hold at most 30'000 multiplications; stack_cap <= 0 means 30000).
+ * out: host int32[7*cap]; *n_out receives the number of entries. When
+ * out == NULL or cap < *n_out only the count is returned. */
+DBCSR_API int dbcsr_get_stacks(char transa, char transb, dbcsr_matrix A, dbcsr_matrix B, int stack_cap,
+                     int *out, int64_t cap, int64_t *n_out);
+
+/* Wait for all work the library queued on its stream. */
+DBCSR_API int dbcsr_sync(void);
+
+/* Message of the last error on the calling thread ("" if none). */
+DBCSR_API const char *dbcsr_last_error(void);
+
+/* Library version string. */
+DBCSR_API const char *dbcsr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DBCSR_GB_H */

@@ -1,0 +1,725 @@
+// api.cu -- the C ABI (include/dbcsr_gb.h): context, allocator, matrix
+// create/release/query and the multiply driver.
+//
+// The multiply follows the paper's local multiplication (Sec. II): build the
+// stacks of block products, execute them with batched small-GEMM kernels, or
+// take the densified path of Sec. III when both operands are dense.
+#include <algorithm>
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <numeric>
+#include <unordered_map>
+
+#include "internal.cuh"
+#include "dense.cuh"
+#include "emul.cuh"
+#include "smm.cuh"
+#include "stackgen.cuh"
+
+namespace dbcsr {
+
+namespace {
+thread_local std::string g_last_error;
+thread_local dbcsr_stats g_stats;
+std::atomic<int64_t> g_launches{0};
+std::atomic<uint64_t> g_uid{1};
+Context g_ctx;
+std::mutex g_init_mutex;
+// allocations made through caller hooks, so each is returned to the hook that made it
+struct HookAlloc {
+    dbcsr_free_fn free;
+    void* ctx;
+};
+std::unordered_map<void*, HookAlloc> g_hook_allocs;
+std::mutex g_hook_mutex;
+}  // namespace
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+int fail(int code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+Context& ctx() { return g_ctx; }
+
+int ensure_device() {
+    if (g_ctx.device >= 0) return DBCSR_OK;
+    std::lock_guard<std::mutex> lk(g_init_mutex);
+    if (g_ctx.device >= 0) return DBCSR_OK;
+    int dev = 0;
+    DB_CUDA(cudaGetDevice(&dev));
+    int sms = 0;
+    DB_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    cudaMemPool_t pool;
+    DB_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
+    uint64_t thr = UINT64_MAX;   // keep freed blocks in the pool (memory-pool buffers, Sec. III)
+    DB_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+    g_ctx.num_sms = sms;
+    g_ctx.device = dev;
+    return DBCSR_OK;
+}
+
+int dev_alloc(void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (g_ctx.alloc) {
+        *p = g_ctx.alloc(bytes, (void*)g_ctx.stream, g_ctx.alloc_ctx);
+        if (!*p) return fail(DBCSR_ERR_ALLOC, "allocator hook returned NULL for " + std::to_string(bytes) + " bytes");
+        std::lock_guard<std::mutex> lk(g_hook_mutex);
+        g_hook_allocs[*p] = HookAlloc{g_ctx.free, g_ctx.alloc_ctx};
+        return DBCSR_OK;
+    }
+    cudaError_t e = cudaMallocAsync(p, bytes, g_ctx.stream);
+    if (e != cudaSuccess || !*p) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(DBCSR_ERR_ALLOC, std::string("device allocation of ") + std::to_string(bytes) +
+                                         " bytes failed: " + cudaGetErrorString(e));
+    }
+    return DBCSR_OK;
+}
+
+void dev_free(void* p, size_t bytes) {
+    if (!p) return;
+    if (bytes == 0) bytes = 16;
+    HookAlloc h{nullptr, nullptr};
+    {
+        std::lock_guard<std::mutex> lk(g_hook_mutex);
+        auto it = g_hook_allocs.find(p);
+        if (it != g_hook_allocs.end()) {
+            h = it->second;
+            g_hook_allocs.erase(it);
+        }
+    }
+    if (h.free) {
+        h.free(p, bytes, (void*)g_ctx.stream, h.ctx);
+        return;
+    }
+    cudaFreeAsync(p, g_ctx.stream);
+}
+
+int h2d(void* dst, const void* src, size_t bytes) {
+    if (bytes) DB_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, g_ctx.stream));
+    return DBCSR_OK;
+}
+int d2h(void* dst, const void* src, size_t bytes) {
+    if (bytes) DB_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, g_ctx.stream));
+    return DBCSR_OK;
+}
+int sync_stream() {
+    DB_CUDA(cudaStreamSynchronize(g_ctx.stream));
+    return DBCSR_OK;
+}
+
+void free_index(dbcsr_matrix_s* m) {
+    dfree(m->d_rowptr, (size_t)m->nbr + 1);
+    dfree(m->d_col, (size_t)(m->nblks ? m->nblks : 1));
+    dfree(m->d_row_of, (size_t)(m->nblks ? m->nblks : 1));
+    dfree(m->d_off, (size_t)m->nblks + 1);
+    dfree(m->d_data, (size_t)(m->nelems ? m->nelems : 1));
+    dfree(m->d_tptr, (size_t)m->nbc + 1);
+    dfree(m->d_tidx, (size_t)(m->nblks ? m->nblks : 1));
+    dfree(m->d_tpos, (size_t)(m->nblks ? m->nblks : 1));
+    m->t_valid = false;
+    m->h_valid = false;
+}
+
+int download_index(dbcsr_matrix_s* m) {
+    if (m->h_valid) return DBCSR_OK;
+    m->h_rowptr.resize(m->nbr + 1);
+    m->h_col.resize(m->nblks);
+    m->h_off.resize(m->nblks + 1);
+    DB_TRY(d2h(m->h_rowptr.data(), m->d_rowptr, sizeof(int) * (m->nbr + 1)));
+    DB_TRY(d2h(m->h_col.data(), m->d_col, sizeof(int) * m->nblks));
+    DB_TRY(d2h(m->h_off.data(), m->d_off, sizeof(int64_t) * (m->nblks + 1)));
+    DB_TRY(sync_stream());
+    m->h_valid = true;
+    return DBCSR_OK;
+}
+
+namespace {
+
+bool is_trans(char t) { return t == 'T' || t == 't' || t == 'C' || t == 'c'; }
+bool valid_trans(char t) { return t == 'N' || t == 'n' || is_trans(t); }
+
+__global__ void k_gather_blocks(int64_t nblks, const int64_t* __restrict__ src_off,
+                                const int64_t* __restrict__ dst_off, const double* __restrict__ src,
+                                double* __restrict__ dst) {
+    for (int64_t b = blockIdx.x; b < nblks; b += gridDim.x) {
+        const int64_t s = src_off[b], d = dst_off[b], n = dst_off[b + 1] - d;
+        for (int64_t e = threadIdx.x; e < n; e += blockDim.x) dst[d + e] = src[s + e];
+    }
+}
+
+// set sizes + offsets (host and device) of a new matrix
+int setup_sizes(dbcsr_matrix_s* m, int nbr, int nbc, const int* rs, const int* cs) {
+    m->nbr = nbr;
+    m->nbc = nbc;
+    m->h_rs.assign(rs, rs + nbr);
+    m->h_cs.assign(cs, cs + nbc);
+    m->h_roff.assign(nbr + 1, 0);
+    m->h_coff.assign(nbc + 1, 0);
+    for (int i = 0; i < nbr; i++) m->h_roff[i + 1] = m->h_roff[i] + rs[i];
+    for (int j = 0; j < nbc; j++) m->h_coff[j + 1] = m->h_coff[j] + cs[j];
+    m->max_rs = nbr ? *std::max_element(rs, rs + nbr) : 0;
+    m->max_cs = nbc ? *std::max_element(cs, cs + nbc) : 0;
+    DB_TRY(dalloc(&m->d_rs, (size_t)nbr + 1));
+    DB_TRY(dalloc(&m->d_cs, (size_t)nbc + 1));
+    DB_TRY(dalloc(&m->d_roff, (size_t)nbr + 1));
+    DB_TRY(dalloc(&m->d_coff, (size_t)nbc + 1));
+    DB_TRY(h2d(m->d_rs, rs, sizeof(int) * nbr));
+    DB_TRY(h2d(m->d_cs, cs, sizeof(int) * nbc));
+    DB_TRY(h2d(m->d_roff, m->h_roff.data(), sizeof(int64_t) * (nbr + 1)));
+    DB_TRY(h2d(m->d_coff, m->h_coff.data(), sizeof(int64_t) * (nbc + 1)));
+    return DBCSR_OK;
+}
+
+void destroy(dbcsr_matrix_s* m) {
+    if (!m) return;
+    free_index(m);
+    dfree(m->d_rs, (size_t)m->nbr + 1);
+    dfree(m->d_cs, (size_t)m->nbc + 1);
+    dfree(m->d_roff, (size_t)m->nbr + 1);
+    dfree(m->d_coff, (size_t)m->nbc + 1);
+    delete m;
+}
+
+// Install a new index + data into m (takes ownership of the device arrays).
+void install(dbcsr_matrix_s* m, int64_t nblks, int64_t nelems, int* rowptr, int* col, int* row_of, int64_t* off,
+             double* data) {
+    free_index(m);
+    m->nblks = nblks;
+    m->nelems = nelems;
+    m->d_rowptr = rowptr;
+    m->d_col = col;
+    m->d_row_of = row_of;
+    m->d_off = off;
+    m->d_data = data;
+    m->version++;
+}
+
+}  // namespace
+}  // namespace dbcsr
+
+using namespace dbcsr;
+
+extern "C" {
+
+const char* dbcsr_last_error(void) { return g_last_error.c_str(); }
+const char* dbcsr_version(void) { return "dbcsr-gb300 0.1 (sm_103a)"; }
+
+int dbcsr_init(void* cuda_stream) {
+    g_last_error.clear();
+    DB_TRY(ensure_device());
+    g_ctx.stream = (cudaStream_t)cuda_stream;
+    return DBCSR_OK;
+}
+
+int dbcsr_set_allocator(dbcsr_alloc_fn alloc, dbcsr_free_fn free_fn, void* actx) {
+    if ((alloc == nullptr) != (free_fn == nullptr))
+        return fail(DBCSR_ERR_ARG, "set_allocator: alloc and free must both be set or both be NULL");
+    g_ctx.alloc = alloc;
+    g_ctx.free = free_fn;
+    g_ctx.alloc_ctx = actx;
+    return DBCSR_OK;
+}
+
+int dbcsr_sync(void) { return sync_stream(); }
+
+int dbcsr_create(dbcsr_matrix* out, int nbr, int nbc, const int* rs, const int* cs, int64_t nblks,
+                 const int* br, const int* bc, const double* data, int data_on_device) {
+    g_last_error.clear();
+    if (!out) return fail(DBCSR_ERR_ARG, "create: out is NULL");
+    *out = nullptr;
+    if (nbr < 0 || nbc < 0 || nblks < 0) return fail(DBCSR_ERR_ARG, "create: negative size");
+    if ((nbr > 0 && !rs) || (nbc > 0 && !cs)) return fail(DBCSR_ERR_ARG, "create: block size array is NULL");
+    if (nblks > 0 && (!br || !bc)) return fail(DBCSR_ERR_ARG, "create: block index array is NULL");
+    if (nblks >= INT32_MAX) return fail(DBCSR_ERR_OVERFLOW, "create: too many blocks");
+    for (int i = 0; i < nbr; i++)
+        if (rs[i] < 1) return fail(DBCSR_ERR_ARG, "create: row block size < 1 at " + std::to_string(i));
+    for (int j = 0; j < nbc; j++)
+        if (cs[j] < 1) return fail(DBCSR_ERR_ARG, "create: col block size < 1 at " + std::to_string(j));
+    for (int64_t b = 0; b < nblks; b++)
+        if (br[b] < 0 || br[b] >= nbr || bc[b] < 0 || bc[b] >= nbc)
+            return fail(DBCSR_ERR_ARG, "create: block coordinate out of range at " + std::to_string(b));
+    DB_TRY(ensure_device());
+
+    // CSR order of the blocks (row, then column), duplicates rejected
+    std::vector<int64_t> perm(nblks);
+    std::iota(perm.begin(), perm.end(), 0);
+    bool sorted = true;
+    for (int64_t b = 1; b < nblks && sorted; b++)
+        if (br[b] < br[b - 1] || (br[b] == br[b - 1] && bc[b] <= bc[b - 1])) sorted = false;
+    if (!sorted) {
+        std::stable_sort(perm.begin(), perm.end(), [&](int64_t x, int64_t y) {
+            return br[x] != br[y] ? br[x] < br[y] : bc[x] < bc[y];
+        });
+        for (int64_t q = 1; q < nblks; q++)
+            if (br[perm[q]] == br[perm[q - 1]] && bc[perm[q]] == bc[perm[q - 1]])
+                return fail(DBCSR_ERR_ARG, "create: duplicate block (" + std::to_string(br[perm[q]]) + "," +
+                                               std::to_string(bc[perm[q]]) + ")");
+    }
+    auto* m = new dbcsr_matrix_s();
+    m->uid = g_uid.fetch_add(1);
+    int rc = setup_sizes(m, nbr, nbc, rs, cs);
+    if (rc) { destroy(m); return rc; }
+    // host index in CSR order
+    std::vector<int> rowptr(nbr + 1, 0), col(nblks), row_of(nblks);
+    std::vector<int64_t> off(nblks + 1, 0), src_off;
+    for (int64_t q = 0; q < nblks; q++) {
+        int64_t b = perm[q];
+        rowptr[br[b] + 1]++;
+        col[q] = bc[b];
+        row_of[q] = br[b];
+        off[q + 1] = off[q] + (int64_t)rs[br[b]] * cs[bc[b]];
+    }
+    for (int i = 0; i < nbr; i++) rowptr[i + 1] += rowptr[i];
+    const int64_t nelems = off[nblks];
+    int *d_rowptr = nullptr, *d_col = nullptr, *d_row_of = nullptr;
+    int64_t* d_off = nullptr;
+    double* d_data = nullptr;
+    if ((rc = dalloc(&d_rowptr, (size_t)nbr + 1)) || (rc = dalloc(&d_col, (size_t)(nblks ? nblks : 1))) ||
+        (rc = dalloc(&d_row_of, (size_t)(nblks ? nblks : 1))) || (rc = dalloc(&d_off, (size_t)nblks + 1)) ||
+        (rc = dalloc(&d_data, (size_t)(nelems ? nelems : 1)))) {
+        dfree(d_rowptr, nbr + 1); dfree(d_col, 1); dfree(d_row_of, 1); dfree(d_off, 1); dfree(d_data, 1);
+        destroy(m);
+        return rc;
+    }
+    install(m, nblks, nelems, d_rowptr, d_col, d_row_of, d_off, d_data);
+    if ((rc = h2d(d_rowptr, rowptr.data(), sizeof(int) * (nbr + 1))) ||
+        (rc = h2d(d_col, col.data(), sizeof(int) * nblks)) ||
+        (rc = h2d(d_row_of, row_of.data(), sizeof(int) * nblks)) ||
+        (rc = h2d(d_off, off.data(), sizeof(int64_t) * (nblks + 1)))) {
+        destroy(m);
+        return rc;
+    }
+    if (!data) {
+        if (nelems) {
+            cudaError_t e = cudaMemsetAsync(d_data, 0, sizeof(double) * nelems, g_ctx.stream);
+            if (e != cudaSuccess) { destroy(m); return fail(DBCSR_ERR_CUDA, cudaGetErrorString(e)); }
+        }
+    } else if (sorted) {
+        cudaError_t e = cudaMemcpyAsync(d_data, data, sizeof(double) * nelems,
+                                        data_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                        g_ctx.stream);
+        if (e != cudaSuccess) { destroy(m); return fail(DBCSR_ERR_CUDA, cudaGetErrorString(e)); }
+    } else {
+        // offsets of the blocks in the caller's order, gathered into CSR order
+        std::vector<int64_t> in_off(nblks + 1, 0);
+        for (int64_t b = 0; b < nblks; b++) in_off[b + 1] = in_off[b] + (int64_t)rs[br[b]] * cs[bc[b]];
+        if (!data_on_device) {
+            std::vector<double> tmp(nelems);
+            for (int64_t q = 0; q < nblks; q++) {
+                int64_t b = perm[q];
+                std::memcpy(tmp.data() + off[q], data + in_off[b], sizeof(double) * (off[q + 1] - off[q]));
+            }
+            if ((rc = h2d(d_data, tmp.data(), sizeof(double) * nelems)) || (rc = sync_stream())) {
+                destroy(m);
+                return rc;
+            }
+        } else {
+            std::vector<int64_t> soff(nblks);
+            for (int64_t q = 0; q < nblks; q++) soff[q] = in_off[perm[q]];
+            DBuf<int64_t> d_soff;
+            if ((rc = d_soff.alloc(nblks)) || (rc = h2d(d_soff.p, soff.data(), sizeof(int64_t) * nblks))) {
+                destroy(m);
+                return rc;
+            }
+            int grid = (int)std::min<int64_t>(nblks, (int64_t)g_ctx.num_sms * 16);
+            k_gather_blocks<<<grid, 256, 0, g_ctx.stream>>>(nblks, d_soff.p, d_off, data, d_data);
+            count_launch();
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) { destroy(m); return fail(DBCSR_ERR_CUDA, cudaGetErrorString(e)); }
+            if ((rc = sync_stream())) { destroy(m); return rc; }
+        }
+    }
+    // host vectors above are sources of async copies: finish before they go
+    if ((rc = sync_stream())) { destroy(m); return rc; }
+    *out = m;
+    return DBCSR_OK;
+}
+
+int dbcsr_release(dbcsr_matrix* m) {
+    if (!m || !*m) return DBCSR_OK;
+    destroy(*m);
+    *m = nullptr;
+    return DBCSR_OK;
+}
+
+int dbcsr_get_info(dbcsr_matrix m, int* nbr, int* nbc, int64_t* nblks, int64_t* nelems) {
+    if (!m) return fail(DBCSR_ERR_ARG, "get_info: NULL matrix");
+    if (nbr) *nbr = m->nbr;
+    if (nbc) *nbc = m->nbc;
+    if (nblks) *nblks = m->nblks;
+    if (nelems) *nelems = m->nelems;
+    return DBCSR_OK;
+}
+
+int dbcsr_get_index(dbcsr_matrix m, int* br, int* bc, int64_t* off) {
+    if (!m) return fail(DBCSR_ERR_ARG, "get_index: NULL matrix");
+    DB_TRY(download_index(m));
+    for (int i = 0; i < m->nbr; i++)
+        for (int q = m->h_rowptr[i]; q < m->h_rowptr[i + 1]; q++) {
+            if (br) br[q] = i;
+            if (bc) bc[q] = m->h_col[q];
+            if (off) off[q] = m->h_off[q];
+        }
+    return DBCSR_OK;
+}
+
+int dbcsr_get_data(dbcsr_matrix m, double* out, int out_on_device) {
+    if (!m || (!out && m->nelems)) return fail(DBCSR_ERR_ARG, "get_data: NULL argument");
+    if (m->nelems == 0) return DBCSR_OK;
+    DB_CUDA(cudaMemcpyAsync(out, m->d_data, sizeof(double) * m->nelems,
+                            out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, g_ctx.stream));
+    if (!out_on_device) DB_TRY(sync_stream());
+    return DBCSR_OK;
+}
+
+int dbcsr_data_ptr(dbcsr_matrix m, double** p) {
+    if (!m || !p) return fail(DBCSR_ERR_ARG, "data_ptr: NULL argument");
+    *p = m->d_data;
+    return DBCSR_OK;
+}
+
+int dbcsr_get_block(dbcsr_matrix m, int row, int col, double* out, int* found) {
+    if (!m || !found) return fail(DBCSR_ERR_ARG, "get_block: NULL argument");
+    *found = 0;
+    if (row < 0 || row >= m->nbr || col < 0 || col >= m->nbc)
+        return fail(DBCSR_ERR_ARG, "get_block: coordinates outside the block grid");
+    DB_TRY(download_index(m));
+    const int* b = m->h_col.data() + m->h_rowptr[row];
+    const int* e = m->h_col.data() + m->h_rowptr[row + 1];
+    const int* it = std::lower_bound(b, e, col);
+    if (it == e || *it != col) return DBCSR_OK;
+    int64_t q = it - m->h_col.data();
+    if (!out) return fail(DBCSR_ERR_ARG, "get_block: out is NULL");
+    DB_TRY(d2h(out, m->d_data + m->h_off[q], sizeof(double) * (m->h_off[q + 1] - m->h_off[q])));
+    DB_TRY(sync_stream());
+    *found = 1;
+    return DBCSR_OK;
+}
+
+int dbcsr_get_stats(dbcsr_stats* out) {
+    if (!out) return fail(DBCSR_ERR_ARG, "get_stats: NULL");
+    *out = g_stats;
+    return DBCSR_OK;
+}
+
+}  // extern "C"
+
+namespace dbcsr {
+namespace {
+
+// CUDA events on the library stream around the phases of one multiply
+struct PhaseTimer {
+    bool on = false;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    void init(bool enable) {
+        on = enable;
+        if (!on) return;
+        for (auto& e : ev)
+            if (cudaEventCreate(&e) != cudaSuccess) on = false;
+    }
+    void mark(int i) {
+        if (on) cudaEventRecord(ev[i], g_ctx.stream);
+    }
+    void finish(dbcsr_stats& s) {
+        if (!on) return;
+        cudaEventSynchronize(ev[3]);
+        cudaEventElapsedTime(&s.ms_setup, ev[0], ev[1]);
+        cudaEventElapsedTime(&s.ms_main, ev[1], ev[2]);
+        cudaEventElapsedTime(&s.ms_finish, ev[2], ev[3]);
+        cudaEventElapsedTime(&s.ms_total, ev[0], ev[3]);
+    }
+    ~PhaseTimer() {
+        for (auto& e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+};
+PhaseTimer* g_timer = nullptr;
+inline void mark(int i) {
+    if (g_timer) g_timer->mark(i);
+}
+
+int check_conformant(bool ta, bool tb, dbcsr_matrix_s* A, dbcsr_matrix_s* B, dbcsr_matrix_s* C) {
+    const std::vector<int>& a_rows = ta ? A->h_cs : A->h_rs;
+    const std::vector<int>& a_cols = ta ? A->h_rs : A->h_cs;
+    const std::vector<int>& b_rows = tb ? B->h_cs : B->h_rs;
+    const std::vector<int>& b_cols = tb ? B->h_rs : B->h_cs;
+    if (a_cols.size() != b_rows.size())
+        return fail(DBCSR_ERR_DIM, "multiply: inner block grids differ (" + std::to_string(a_cols.size()) + " vs " +
+                                       std::to_string(b_rows.size()) + ")");
+    if (a_rows.size() != C->h_rs.size() || b_cols.size() != C->h_cs.size())
+        return fail(DBCSR_ERR_DIM, "multiply: C block grid does not match op(A) x op(B)");
+    if (a_cols != b_rows) return fail(DBCSR_ERR_DIM, "multiply: inner block sizes of op(A) and op(B) differ");
+    if (a_rows != C->h_rs || b_cols != C->h_cs)
+        return fail(DBCSR_ERR_DIM, "multiply: C block sizes do not match op(A) x op(B)");
+    return DBCSR_OK;
+}
+
+double useful_flops_host(bool ta, bool tb, dbcsr_matrix_s* A, dbcsr_matrix_s* B, int64_t* nprod) {
+    // sum over k of (2 * k_size * sum_{i in col k of op A} m_i * sum_{j in row k of op B} n_j)
+    // computed on the host from the downloaded indices
+    download_index(A);
+    download_index(B);
+    const int nk = ta ? A->nbr : A->nbc;
+    std::vector<double> am(nk, 0.0), bn(nk, 0.0);
+    std::vector<int64_t> ac(nk, 0), bc(nk, 0);
+    for (int i = 0; i < A->nbr; i++)
+        for (int q = A->h_rowptr[i]; q < A->h_rowptr[i + 1]; q++) {
+            int j = A->h_col[q];
+            int k = ta ? i : j;
+            int mm = ta ? A->h_cs[j] : A->h_rs[i];
+            am[k] += mm;
+            ac[k]++;
+        }
+    for (int i = 0; i < B->nbr; i++)
+        for (int q = B->h_rowptr[i]; q < B->h_rowptr[i + 1]; q++) {
+            int j = B->h_col[q];
+            int k = tb ? j : i;
+            int nn = tb ? B->h_rs[i] : B->h_cs[j];
+            bn[k] += nn;
+            bc[k]++;
+        }
+    double f = 0.0;
+    int64_t np = 0;
+    const std::vector<int>& ks = ta ? A->h_rs : A->h_cs;
+    for (int k = 0; k < nk; k++) {
+        f += 2.0 * ks[k] * am[k] * bn[k];
+        np += ac[k] * bc[k];
+    }
+    if (nprod) *nprod = np;
+    return f;
+}
+
+int multiply_stacks(bool ta, bool tb, double alpha, dbcsr_matrix_s* A, dbcsr_matrix_s* B, double beta,
+                    dbcsr_matrix_s* C, const dbcsr_opts& o) {
+    if (ta) DB_TRY(build_transpose_index(A));
+    if (tb) DB_TRY(build_transpose_index(B));
+    OpView va = make_view(A, ta), vb = make_view(B, tb);
+    const bool use_old = beta != 0.0 && C->nblks > 0;
+    StackPlan P;
+    mark(0);
+    DB_TRY(build_stacks(va, vb, use_old ? C : nullptr, C->d_rs, C->d_cs, P));
+    double* data = nullptr;
+    DB_TRY(dalloc(&data, (size_t)(P.nelem ? P.nelem : 1)));
+    DBuf<unsigned long long> counter;
+    DB_TRY(counter.alloc(1));
+    DB_CUDA(cudaMemsetAsync(counter.p, 0, sizeof(unsigned long long), g_ctx.stream));
+    SmmArgs g;
+    g.nC = P.nC;
+    g.c_row = P.c_row;
+    g.c_col = P.c_col;
+    g.c_off = P.c_off;
+    g.c_old = use_old ? P.c_old : nullptr;
+    g.c_pstart = P.c_pstart;
+    g.prod = P.prod;
+    g.A = va;
+    g.B = vb;
+    g.rsC = C->d_rs;
+    g.csC = C->d_cs;
+    g.Cd = data;
+    g.Cold = use_old ? C->d_data : nullptr;
+    g.Cold_off = use_old ? C->d_off : nullptr;
+    g.alpha = alpha;
+    g.beta = beta;
+    g.counter = counter.p;
+    int rc;
+    mark(1);
+    if (o.precision == DBCSR_PREC_FP64) {
+        rc = smm_fp64_generic(g, C->max_rs * C->max_cs);
+        g_stats.main_flops = g_stats.useful_flops;
+    } else {
+        rc = smm_emulated(g, C->max_rs, C->max_cs, std::max(A->max_rs, A->max_cs), o);
+    }
+    mark(2);
+    if (rc) { dfree(data, (size_t)(P.nelem ? P.nelem : 1)); return rc; }
+    // minimal traffic: every stored A and B block read once, C written once (+ read once)
+    g_stats.main_bytes = 8.0 * ((double)A->nelems + (double)B->nelems + (double)P.nelem +
+                                (use_old ? (double)C->nelems : 0.0));
+    g_stats.n_products = P.nprod;
+    g_stats.c_blocks = P.nC;
+    // hand C the new index (the plan's arrays change owner)
+    int* rowptr = P.c_rowptr;
+    int* col = P.c_col;
+    int* row_of = P.c_row;
+    int64_t* off = P.c_off;
+    P.c_rowptr = nullptr;
+    P.c_col = nullptr;
+    P.c_row = nullptr;
+    P.c_off = nullptr;
+    const int64_t nC = P.nC, ne = P.nelem;
+    P.nC = 0;   // arrays above no longer belong to P
+    dfree(P.c_old, (size_t)(nC ? nC : 1));
+    dfree(P.c_pstart, (size_t)nC + 1);
+    install(C, nC, ne, rowptr, col, row_of, off, data);
+    mark(3);
+    return DBCSR_OK;
+}
+
+__global__ void k_full_index(int nbr, int nbc, const int* __restrict__ rs, const int* __restrict__ cs,
+                             const int64_t* __restrict__ roff, const int64_t* __restrict__ coff, int64_t N,
+                             int* __restrict__ rowptr, int* __restrict__ col, int* __restrict__ row_of,
+                             int64_t* __restrict__ off) {
+    int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t nb = (int64_t)nbr * nbc;
+    if (b < nb) {
+        int i = (int)(b / nbc), j = (int)(b % nbc);
+        col[b] = j;
+        row_of[b] = i;
+        off[b] = roff[i] * N + (int64_t)rs[i] * coff[j];
+    }
+    if (b <= nbr && b >= 0) rowptr[b] = (int)(b * nbc);
+    if (b == 0) off[nb] = roff[nbr] * N;
+}
+
+int multiply_dense(bool ta, bool tb, double alpha, dbcsr_matrix_s* A, dbcsr_matrix_s* B, double beta,
+                   dbcsr_matrix_s* C, const dbcsr_opts& o) {
+    const int64_t M = C->h_roff[C->nbr], N = C->h_coff[C->nbc];
+    const int64_t K = ta ? A->h_roff[A->nbr] : A->h_coff[A->nbc];
+    const bool a_full = A->nblks == (int64_t)A->nbr * A->nbc;
+    const bool b_full = B->nblks == (int64_t)B->nbr * B->nbc;
+    const bool use_old = beta != 0.0 && C->nblks > 0;
+    const int nbk = ta ? A->nbr : A->nbc;
+    // result pattern: full when both operands are full (and K > 0); else the
+    // symbolic product (through stack generation's pattern pass)
+    DBuf<double> dA, dB, dC;
+    mark(0);
+    DB_TRY(dA.alloc((size_t)std::max<int64_t>(M * K, 1)));
+    DB_TRY(dB.alloc((size_t)std::max<int64_t>(K * N, 1)));
+    DB_TRY(dC.alloc((size_t)std::max<int64_t>(M * N, 1)));
+    DB_TRY(densify(A, ta, dA.p, M, !a_full));
+    DB_TRY(densify(B, tb, dB.p, K, !b_full));
+    if (use_old) DB_TRY(densify(C, false, dC.p, M, C->nblks != (int64_t)C->nbr * C->nbc));
+    const double beta_eff = use_old ? beta : 0.0;
+    mark(1);
+    if (o.precision == DBCSR_PREC_FP64) {
+        DB_TRY(dgemm_fp64(M, N, K, alpha, dA.p, M, dB.p, K, beta_eff, dC.p, M));
+        g_stats.main_flops = 2.0 * (double)M * (double)N * (double)K;
+    } else {
+        DB_TRY(dgemm_emulated(M, N, K, alpha, dA.p, M, dB.p, K, beta_eff, dC.p, M, o));
+    }
+    mark(2);
+    if (o.precision != DBCSR_PREC_OZAKI)
+        g_stats.main_bytes = 8.0 * ((double)M * K + (double)K * N + (double)M * N * (beta_eff != 0.0 ? 2 : 1));
+    // new C index
+    if (a_full && b_full && nbk > 0) {
+        const bool same = C->nblks == (int64_t)C->nbr * C->nbc;   // old C already full, CSR-ordered
+        if (!same) {
+            const int64_t nb = (int64_t)C->nbr * C->nbc;
+            if (nb >= INT32_MAX) return fail(DBCSR_ERR_OVERFLOW, "multiply: result has too many blocks");
+            int *rowptr = nullptr, *col = nullptr, *row_of = nullptr;
+            int64_t* off = nullptr;
+            double* data = nullptr;
+            DB_TRY(dalloc(&rowptr, (size_t)C->nbr + 1));
+            DB_TRY(dalloc(&col, (size_t)nb));
+            DB_TRY(dalloc(&row_of, (size_t)nb));
+            DB_TRY(dalloc(&off, (size_t)nb + 1));
+            DB_TRY(dalloc(&data, (size_t)(M * N)));
+            int64_t cnt = std::max<int64_t>(nb, C->nbr + 1);
+            k_full_index<<<(unsigned)cdiv(cnt, 256), 256, 0, g_ctx.stream>>>(
+                C->nbr, C->nbc, C->d_rs, C->d_cs, C->d_roff, C->d_coff, N, rowptr, col, row_of, off);
+            DB_KCHECK();
+            install(C, nb, M * N, rowptr, col, row_of, off, data);
+        }
+        DB_TRY(undensify(C, dC.p, M));
+        mark(3);
+        g_stats.c_blocks = C->nblks;
+        return DBCSR_OK;
+    }
+    // sparse operands forced onto the dense path: pattern from the symbolic pass
+    if (ta) DB_TRY(build_transpose_index(A));
+    if (tb) DB_TRY(build_transpose_index(B));
+    OpView va = make_view(A, ta), vb = make_view(B, tb);
+    StackPlan P;
+    DB_TRY(build_stacks(va, vb, use_old ? C : nullptr, C->d_rs, C->d_cs, P));
+    double* data = nullptr;
+    DB_TRY(dalloc(&data, (size_t)(P.nelem ? P.nelem : 1)));
+    const int64_t nC = P.nC, ne = P.nelem;
+    install(C, nC, ne, P.c_rowptr, P.c_col, P.c_row, P.c_off, data);
+    P.c_rowptr = nullptr;
+    P.c_col = nullptr;
+    P.c_row = nullptr;
+    P.c_off = nullptr;
+    P.nC = 0;
+    dfree(P.c_old, (size_t)(nC ? nC : 1));
+    dfree(P.c_pstart, (size_t)nC + 1);
+    DB_TRY(undensify(C, dC.p, M));
+    mark(3);
+    g_stats.c_blocks = nC;
+    return DBCSR_OK;
+}
+
+}  // namespace
+}  // namespace dbcsr
+
+extern "C" int dbcsr_multiply(char transa, char transb, double alpha, dbcsr_matrix A, dbcsr_matrix B, double beta,
+                              dbcsr_matrix C, const dbcsr_opts* opts) {
+    g_last_error.clear();
+    if (!A || !B || !C) return fail(DBCSR_ERR_ARG, "multiply: NULL matrix");
+    if (C == A || C == B) return fail(DBCSR_ERR_ARG, "multiply: C must differ from A and B");
+    if (!valid_trans(transa) || !valid_trans(transb))
+        return fail(DBCSR_ERR_ARG, "multiply: trans must be 'N', 'T' or 'C'");
+    dbcsr_opts o{};
+    if (opts) o = *opts;
+    if (o.path < 0 || o.path > 2 || o.precision < 0 || o.precision > 2 || o.ozaki_slices < 0 || o.ozaki_slices > 12)
+        return fail(DBCSR_ERR_ARG, "multiply: invalid options");
+    DB_TRY(ensure_device());
+    const bool ta = is_trans(transa), tb = is_trans(transb);
+    DB_TRY(check_conformant(ta, tb, A, B, C));
+    const int64_t launches0 = g_launches.load();
+    std::memset(&g_stats, 0, sizeof(g_stats));
+    int64_t np = 0;
+    g_stats.useful_flops = useful_flops_host(ta, tb, A, B, &np);
+    g_stats.n_products = np;
+    int path = o.path;
+    if (path == DBCSR_PATH_AUTO) {
+        const bool a_full = A->nblks == (int64_t)A->nbr * A->nbc && A->nblks > 0;
+        const bool b_full = B->nblks == (int64_t)B->nbr * B->nbc && B->nblks > 0;
+        path = (a_full && b_full) ? DBCSR_PATH_DENSE : DBCSR_PATH_STACKS;
+    }
+    g_stats.path = path;
+    g_stats.precision = o.precision;
+    PhaseTimer timer;
+    timer.init(o.timing != 0);
+    g_timer = timer.on ? &timer : nullptr;
+    int rc = (path == DBCSR_PATH_DENSE) ? multiply_dense(ta, tb, alpha, A, B, beta, C, o)
+                                        : multiply_stacks(ta, tb, alpha, A, B, beta, C, o);
+    g_timer = nullptr;
+    if (rc == DBCSR_OK) rc = sync_stream();
+    if (rc == DBCSR_OK) timer.finish(g_stats);
+    g_stats.kernel_launches = (int)(g_launches.load() - launches0);
+    C->h_valid = false;
+    C->t_valid = false;
+    return rc;
+}
+
+extern "C" int dbcsr_get_stacks(char transa, char transb, dbcsr_matrix A, dbcsr_matrix B, int stack_cap, int* out,
+                                int64_t cap, int64_t* n_out) {
+    g_last_error.clear();
+    if (!A || !B || !n_out) return fail(DBCSR_ERR_ARG, "get_stacks: NULL argument");
+    if (!valid_trans(transa) || !valid_trans(transb))
+        return fail(DBCSR_ERR_ARG, "get_stacks: trans must be 'N', 'T' or 'C'");
+    DB_TRY(ensure_device());
+    const bool ta = is_trans(transa), tb = is_trans(transb);
+    const std::vector<int>& a_cols = ta ? A->h_rs : A->h_cs;
+    const std::vector<int>& b_rows = tb ? B->h_cs : B->h_rs;
+    if (a_cols != b_rows) return fail(DBCSR_ERR_DIM, "get_stacks: inner block sizes differ");
+    if (ta) DB_TRY(build_transpose_index(A));
+    if (tb) DB_TRY(build_transpose_index(B));
+    OpView va = make_view(A, ta), vb = make_view(B, tb);
+    StackPlan P;
+    DB_TRY(build_stacks(va, vb, nullptr, va.rs, vb.cs, P));
+    *n_out = P.nprod;
+    std::vector<int> sizes;
+    sizes.insert(sizes.end(), A->h_rs.begin(), A->h_rs.end());
+    sizes.insert(sizes.end(), A->h_cs.begin(), A->h_cs.end());
+    sizes.insert(sizes.end(), B->h_rs.begin(), B->h_rs.end());
+    sizes.insert(sizes.end(), B->h_cs.begin(), B->h_cs.end());
+    int64_t nst = 0, nsh = 0;
+    if (out && cap >= P.nprod) DB_TRY(export_stacks(va, P, va.rs, vb.cs, sizes, stack_cap, out, &nst, &nsh));
+    return DBCSR_OK;
+}

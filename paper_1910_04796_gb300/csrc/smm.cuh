@@ -1,0 +1,29 @@
+// smm.cuh -- arguments of the batched small-matrix product kernels.
+#pragma once
+#include "internal.cuh"
+
+namespace dbcsr {
+
+// One launch covers every C block of the plan: C block cb = (c_row, c_col) at
+// element offset c_off, its products prod[c_pstart[cb] .. c_pstart[cb+1]).
+struct SmmArgs {
+    int64_t nC;
+    const int* c_row;
+    const int* c_col;
+    const int64_t* c_off;
+    const int* c_old;          // stored position in old C, -1 none (nullptr: no old C)
+    const int64_t* c_pstart;
+    const int2* prod;
+    OpView A, B;               // op(A), op(B); off[] has a sentinel entry at nblks
+    const int* rsC;
+    const int* csC;
+    double* Cd;                // new C data
+    const double* Cold;        // old C data (beta != 0)
+    const int64_t* Cold_off;
+    double alpha, beta;
+    unsigned long long* counter;  // zeroed work counter
+};
+
+int smm_fp64_generic(const SmmArgs& g, int max_mn);
+
+}  // namespace dbcsr
