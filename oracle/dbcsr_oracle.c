@@ -419,3 +419,129 @@ int oracle_num_threads(void)
     return 1;
 #endif
 }
+
+/* ---------------------------------------------------------------------------
+ * Emulated FP64 product with integer slices (not in the paper: the precision
+ * form of the dense / large-block path). Scheme: Ozaki, Ogita, Oishi & Rump
+ * (2012), error-free splitting, in its integer form (Ootomo, Ozaki & Yokota
+ * 2024), stated here step by step:
+ *
+ *  1. Row scaling of A: mu_i = max_l |A(i,l)|, e_i = the exponent with
+ *     mu_i = f * 2^e_i, 1/2 <= f < 1 (frexp), so |A(i,l)| * 2^-e_i < 1.
+ *     e_i = 0 for a zero row. Column scaling of B likewise, exponents f_j.
+ *  2. Slices by truncation: x = A(i,l) * 2^-e_i, r_0 = x, and for
+ *     t = 1..s:  sigma_t = trunc(r_{t-1} * 2^(7t)),
+ *                r_t = r_{t-1} - sigma_t * 2^(-7t).
+ *     Every sigma_t is an integer in [-127, 127] with the sign of x; every
+ *     step is exact in FP64. So x = sum_t sigma_t 2^(-7t) + r_s, |r_s| < 2^-7s.
+ *  3. Integer products, kept exactly: for each level d = t + u with
+ *     2 <= d <= s+1 (the triangular truncation: pairs with t + u > s + 1 are
+ *     dropped), G_d(i,j) = sum over t+u=d of sum_l sigmaA_t(i,l) sigmaB_u(l,j).
+ *  4. Recombination in FP64, smallest level first:
+ *     acc = 0; for d = s+1 down to 2: acc = acc + G_d * 2^(-7d)
+ *     (each term exact, one rounding per sum).
+ *  5. C(i,j) = alpha * (acc * 2^(e_i + f_j)) + beta * C(i,j).
+ * ------------------------------------------------------------------------- */
+static int frexp_exp(double mu)
+{
+    int e = 0;
+    if (mu == 0.0) return 0;
+    (void)frexp(mu, &e);
+    return e;
+}
+
+/* slices of one pre-scaled value x (|x| < 1): out[t-1] = sigma_t */
+void oracle_ozaki_split(double x, int s, int *out)
+{
+    double r = x;
+    for (int t = 1; t <= s; t++) {
+        double sg = trunc(ldexp(r, 7 * t));
+        out[t - 1] = (int)sg;
+        r = r - ldexp(sg, -7 * t);
+    }
+}
+
+/* row exponents of column-major A (M x K), column exponents of column-major B (K x N) */
+void oracle_ozaki_exponents(int64_t M, int64_t N, int64_t K, const double *A, int64_t lda,
+                            const double *B, int64_t ldb, int *e_row, int *f_col)
+{
+    for (int64_t i = 0; i < M; i++) {
+        double mu = 0.0;
+        for (int64_t l = 0; l < K; l++) { double v = fabs(A[i + l * lda]); if (v > mu) mu = v; }
+        e_row[i] = frexp_exp(mu);
+    }
+    for (int64_t j = 0; j < N; j++) {
+        double nu = 0.0;
+        for (int64_t l = 0; l < K; l++) { double v = fabs(B[l + j * ldb]); if (v > nu) nu = v; }
+        f_col[j] = frexp_exp(nu);
+    }
+}
+
+/* The emulated product on column-major operands; only the rows in rows_sel
+ * (NULL = all) of C are computed and written. Optionally returns the level
+ * sums G_d (int64, [s][nsel][N] row-major per level) for slice-level checks. */
+int oracle_ozaki_gemm(int64_t M, int64_t N, int64_t K, double alpha, const double *A, int64_t lda,
+                      const double *B, int64_t ldb, double beta, double *C, int64_t ldc, int s,
+                      const int *rows_sel, int nrows_sel, int nthreads, int64_t *levels_out)
+{
+    if (s < 1 || s > 8) return -1;
+    int *e_row = (int *)malloc(sizeof(int) * (size_t)(M + 1));
+    int *f_col = (int *)malloc(sizeof(int) * (size_t)(N + 1));
+    /* slices of B, stored [u][l][j] (j fastest) */
+    signed char *SB = (signed char *)malloc((size_t)s * (size_t)K * (size_t)N + 1);
+    if (!e_row || !f_col || !SB) { free(e_row); free(f_col); free(SB); return -1; }
+    oracle_ozaki_exponents(M, N, K, A, lda, B, ldb, e_row, f_col);
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+#pragma omp parallel for schedule(static)
+    for (int64_t j = 0; j < N; j++) {
+        int sl[8];
+        for (int64_t l = 0; l < K; l++) {
+            oracle_ozaki_split(ldexp(B[l + j * ldb], -f_col[j]), s, sl);
+            for (int u = 0; u < s; u++) SB[((size_t)u * K + l) * N + j] = (signed char)sl[u];
+        }
+    }
+    int nsel = rows_sel ? nrows_sel : (int)M;
+#pragma omp parallel
+    {
+        signed char *SA = (signed char *)malloc((size_t)s * (size_t)K + 1);
+        int64_t *G = (int64_t *)malloc(sizeof(int64_t) * (size_t)(s + 2) * (size_t)N);
+#pragma omp for schedule(dynamic, 1)
+        for (int q = 0; q < nsel; q++) {
+            int64_t i = rows_sel ? rows_sel[q] : q;
+            int sl[8];
+            for (int64_t l = 0; l < K; l++) {
+                oracle_ozaki_split(ldexp(A[i + l * lda], -e_row[i]), s, sl);
+                for (int t = 0; t < s; t++) SA[(size_t)t * K + l] = (signed char)sl[t];
+            }
+            memset(G, 0, sizeof(int64_t) * (size_t)(s + 2) * (size_t)N);
+            for (int t = 1; t <= s; t++)
+                for (int u = 1; u + t <= s + 1; u++) {
+                    int64_t *g = G + (size_t)(t + u) * N;
+                    for (int64_t l = 0; l < K; l++) {
+                        int64_t a = SA[(size_t)(t - 1) * K + l];
+                        if (a == 0) continue;
+                        const signed char *b = SB + ((size_t)(u - 1) * K + l) * N;
+                        for (int64_t j = 0; j < N; j++) g[j] += a * (int64_t)b[j];
+                    }
+                }
+            for (int64_t j = 0; j < N; j++) {
+                double acc = 0.0;
+                for (int d = s + 1; d >= 2; d--) acc = acc + ldexp((double)G[(size_t)d * N + j], -7 * d);
+                double v = alpha * ldexp(acc, e_row[i] + f_col[j]);
+                if (beta != 0.0) v = v + beta * C[i + j * ldc];
+                C[i + j * ldc] = v;
+            }
+            if (levels_out)
+                for (int d = 2; d <= s + 1; d++)
+                    memcpy(levels_out + ((size_t)(d - 2) * nsel + q) * N, G + (size_t)d * N,
+                           sizeof(int64_t) * (size_t)N);
+        }
+        free(SA); free(G);
+    }
+    free(e_row); free(f_col); free(SB);
+    return 0;
+}

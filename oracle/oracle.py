@@ -212,3 +212,72 @@ def normwise_error(Cd, Cref, Ad, Bd) -> float:
     """||C - C_ref||_F / (||A||_F * ||B||_F), the accuracy measure used throughout."""
     den = np.linalg.norm(Ad) * np.linalg.norm(Bd)
     return float(np.linalg.norm(np.asarray(Cd) - np.asarray(Cref)) / (den if den > 0 else 1.0))
+
+
+# --------------------------------------------------------------------------
+# Emulated FP64 with 7-bit integer slices (Ozaki et al. 2012, integer form):
+# row/column power-of-two scaling, truncated slices, exact integer level sums
+# G_d (d = t + u <= s + 1), FP64 recombination from the smallest level up.
+# --------------------------------------------------------------------------
+def _ozaki_sigs():
+    L = lib()
+    if getattr(L, "_oz_ready", False):
+        return L
+    L.oracle_ozaki_split.restype = None
+    L.oracle_ozaki_split.argtypes = [C.c_double, C.c_int, C.POINTER(C.c_int)]
+    L.oracle_ozaki_exponents.restype = None
+    L.oracle_ozaki_exponents.argtypes = [C.c_int64, C.c_int64, C.c_int64, C.POINTER(C.c_double), C.c_int64,
+                                         C.POINTER(C.c_double), C.c_int64, C.POINTER(C.c_int),
+                                         C.POINTER(C.c_int)]
+    L.oracle_ozaki_gemm.restype = C.c_int
+    L.oracle_ozaki_gemm.argtypes = [C.c_int64, C.c_int64, C.c_int64, C.c_double, C.POINTER(C.c_double), C.c_int64,
+                                    C.POINTER(C.c_double), C.c_int64, C.c_double, C.POINTER(C.c_double),
+                                    C.c_int64, C.c_int, C.POINTER(C.c_int), C.c_int, C.c_int,
+                                    C.POINTER(C.c_int64)]
+    L._oz_ready = True
+    return L
+
+
+def ozaki_split(x: float, s: int):
+    """Slices sigma_1..sigma_s of one pre-scaled value |x| < 1."""
+    out = (C.c_int * s)()
+    _ozaki_sigs().oracle_ozaki_split(float(x), s, out)
+    return list(out)
+
+
+def ozaki_exponents(Ad, Bd):
+    Ad = np.asfortranarray(Ad, np.float64)
+    Bd = np.asfortranarray(Bd, np.float64)
+    M, K = Ad.shape
+    N = Bd.shape[1]
+    e = np.zeros(max(M, 1), np.int32)
+    f = np.zeros(max(N, 1), np.int32)
+    _ozaki_sigs().oracle_ozaki_exponents(M, N, K, _dp(Ad), max(M, 1), _dp(Bd), max(K, 1), _ip(e), _ip(f))
+    return e[:M], f[:N]
+
+
+def ozaki_gemm(alpha, Ad, Bd, beta, Cd, s=7, rows=None, nthreads=0, want_levels=False):
+    """Emulated C = alpha*A*B + beta*C on dense column-major arrays (updates Cd).
+
+    rows: only these rows of C are computed (the others are left as they are).
+    Returns (Cd, levels) with levels[d-2][q][j] = G_d for the selected rows.
+    """
+    Ad = np.asfortranarray(Ad, np.float64)
+    Bd = np.asfortranarray(Bd, np.float64)
+    assert Cd.flags.f_contiguous and Cd.dtype == np.float64
+    M, K = Ad.shape
+    N = Bd.shape[1]
+    rp, nr = None, 0
+    keep = []
+    if rows is not None:
+        r = np.ascontiguousarray(np.unique(np.asarray(rows, np.int32)))
+        keep.append(r)
+        rp, nr = _ip(r), len(r)
+    nsel = nr if rows is not None else M
+    lv = np.zeros((s, max(nsel, 1), max(N, 1)), np.int64) if want_levels else None
+    rc = _ozaki_sigs().oracle_ozaki_gemm(M, N, K, alpha, _dp(Ad), max(M, 1), _dp(Bd), max(K, 1), beta, _dp(Cd),
+                                         max(M, 1), s, rp, nr, nthreads,
+                                         lv.ctypes.data_as(C.POINTER(C.c_int64)) if lv is not None else None)
+    if rc != 0:
+        raise ValueError("oracle_ozaki_gemm failed")
+    return Cd, lv

@@ -1,0 +1,127 @@
+"""Pins of the oracle's emulated-FP64 (integer-slice) product (CPU only).
+
+The emulation is not in the paper; it follows Ozaki, Ogita, Oishi & Rump
+(2012) in integer form. Pinned against: exact integer arithmetic (inputs that
+the leading slice captures whole), exact rational arithmetic within the
+method's own truncation bound, the exact reconstruction of a value from 8
+slices of 7 bits (56 >= 53 bits), monotone error decrease in the slice count,
+and the level-sum identity against an int64 matmul of slices built here.
+"""
+from fractions import Fraction
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+
+
+def test_split_properties():
+    rng = np.random.default_rng(50)
+    for x in rng.uniform(-1, 1, 200):
+        sl = O.ozaki_split(x, 8)
+        assert all(-127 <= v <= 127 for v in sl)
+        assert all(v == 0 or (v > 0) == (x > 0) for v in sl)       # truncation keeps the sign
+        rec = sum(Fraction(v) * Fraction(2) ** (-7 * (t + 1)) for t, v in enumerate(sl))
+        if abs(x) >= 2 ** -4:                                      # 53 bits all inside 56
+            assert rec == Fraction(float(x))
+        r5 = sum(Fraction(v) * Fraction(2) ** (-7 * (t + 1)) for t, v in enumerate(O.ozaki_split(x, 5)))
+        assert abs(Fraction(float(x)) - r5) < Fraction(2) ** -35   # |r_s| < 2^-7s
+        assert abs(r5) <= abs(Fraction(float(x)))                  # truncation toward zero
+
+
+def test_split_known_values():
+    # 0.5 = 64 * 2^-7; -0.75 = -96 * 2^-7; 2^-8 = 64 * 2^-14
+    assert O.ozaki_split(0.5, 3) == [64, 0, 0]
+    assert O.ozaki_split(-0.75, 3) == [-96, 0, 0]
+    assert O.ozaki_split(2.0 ** -8, 3) == [0, 64, 0]
+    assert O.ozaki_split(1 - 2.0 ** -21, 3) == [127, 127, 127]
+
+
+def test_exponents_frexp():
+    A = np.asfortranarray(np.array([[0.5, -3.0], [0.0, 0.0], [1.0, 0.25]]))
+    B = np.asfortranarray(np.array([[7.9, 0.0], [-8.0, 0.0]]))
+    e, f = O.ozaki_exponents(A, B)
+    assert list(e) == [2, 0, 1]       # 3 = 0.75*2^2; zero row -> 0; 1 = 0.5*2^1
+    assert list(f) == [4, 0]          # 8 = 0.5*2^4
+
+
+@pytest.mark.parametrize("s", [1, 3, 7])
+def test_integer_inputs_exact(s):
+    rng = np.random.default_rng(51)
+    A = rng.integers(-8, 9, (17, 23)).astype(np.float64)
+    B = rng.integers(-8, 9, (23, 13)).astype(np.float64)
+    Cd = np.zeros((17, 13), order="F")
+    O.ozaki_gemm(1.0, A, B, 0.0, Cd, s=s)
+    assert np.array_equal(Cd, A @ B)
+
+
+def test_levels_equal_int_matmul_of_slices():
+    rng = np.random.default_rng(52)
+    M, K, N, s = 6, 9, 5, 4
+    A = np.asfortranarray(rng.uniform(-1, 1, (M, K)))
+    B = np.asfortranarray(rng.uniform(-1, 1, (K, N)))
+    e, f = O.ozaki_exponents(A, B)
+    SA = np.zeros((s, M, K), np.int64)
+    SB = np.zeros((s, K, N), np.int64)
+    for i in range(M):
+        for l in range(K):
+            SA[:, i, l] = O.ozaki_split(math.ldexp(A[i, l], -int(e[i])), s)
+    for l in range(K):
+        for j in range(N):
+            SB[:, l, j] = O.ozaki_split(math.ldexp(B[l, j], -int(f[j])), s)
+    _, lv = O.ozaki_gemm(1.0, A, B, 0.0, np.zeros((M, N), order="F"), s=s, want_levels=True)
+    for d in range(2, s + 2):
+        G = sum(SA[t - 1] @ SB[d - t - 1] for t in range(1, d) if 1 <= d - t <= s)
+        assert np.array_equal(lv[d - 2], G)
+
+
+def test_error_within_truncation_bound_exact_rationals():
+    rng = np.random.default_rng(53)
+    M, K, N = 5, 30, 4
+    A = np.asfortranarray(rng.uniform(-1, 1, (M, K)) * 10.0 ** rng.uniform(-4, 4, (M, K)))
+    B = np.asfortranarray(rng.uniform(-1, 1, (K, N)) * 10.0 ** rng.uniform(-4, 4, (K, N)))
+    e, f = O.ozaki_exponents(A, B)
+    for s in (3, 5, 7):
+        Cd = np.zeros((M, N), order="F")
+        O.ozaki_gemm(1.0, A, B, 0.0, Cd, s=s)
+        for i in range(M):
+            for j in range(N):
+                exact = sum(Fraction(float(A[i, l])) * Fraction(float(B[l, j])) for l in range(K))
+                # per scaled product: truncation (2.01 * 2^-7s) + dropped levels (s * 2^-7s)
+                trunc = Fraction(2) ** (int(e[i]) + int(f[j])) * K * (Fraction(s) + Fraction(201, 100)) \
+                    * Fraction(2) ** (-7 * s)
+                rounding = Fraction(2) ** -50 * (abs(exact) + Fraction(2) ** (int(e[i]) + int(f[j])) * K)
+                assert abs(Fraction(float(Cd[i, j])) - exact) <= trunc + rounding
+
+
+def test_error_decreases_with_slices_and_meets_1e12():
+    rng = np.random.default_rng(54)
+    M = K = N = 64
+    A = np.asfortranarray(rng.uniform(-1, 1, (M, K)) * 10.0 ** rng.uniform(-4, 4, (M, K)))
+    B = np.asfortranarray(rng.uniform(-1, 1, (K, N)) * 10.0 ** rng.uniform(-4, 4, (K, N)))
+    ref = np.zeros((M, N), order="F")
+    O.dense_gemm("N", "N", 1.0, A, B, 0.0, ref)
+    errs = []
+    for s in range(2, 9):
+        Cd = np.zeros((M, N), order="F")
+        O.ozaki_gemm(1.0, A, B, 0.0, Cd, s=s)
+        errs.append(O.normwise_error(Cd, ref, A, B))
+    assert all(errs[q + 1] <= errs[q] * 1.0001 + 1e-17 for q in range(len(errs) - 1))
+    assert errs[7 - 2] <= 1e-12
+
+
+def test_alpha_beta_and_row_subset():
+    rng = np.random.default_rng(55)
+    A = np.asfortranarray(rng.uniform(-1, 1, (9, 11)))
+    B = np.asfortranarray(rng.uniform(-1, 1, (11, 7)))
+    C0 = np.asfortranarray(rng.uniform(-1, 1, (9, 7)))
+    full = C0.copy(order="F")
+    O.ozaki_gemm(0.5, A, B, 2.0, full, s=6)
+    base = np.zeros((9, 7), order="F")
+    O.ozaki_gemm(1.0, A, B, 0.0, base, s=6)
+    assert np.array_equal(full, (0.5 * base) + (2.0 * C0))
+    sub = C0.copy(order="F")
+    O.ozaki_gemm(0.5, A, B, 2.0, sub, s=6, rows=[1, 4])
+    assert np.array_equal(sub[[1, 4]], full[[1, 4]])
+    assert np.array_equal(np.delete(sub, [1, 4], 0), np.delete(C0, [1, 4], 0))
