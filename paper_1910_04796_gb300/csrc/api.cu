@@ -57,6 +57,8 @@ int ensure_device() {
     uint64_t thr = UINT64_MAX;   // keep freed blocks in the pool (memory-pool buffers, Sec. III)
     DB_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
     g_ctx.num_sms = sms;
+    cudaError_t e = cudaMalloc(&g_ctx.d_flags, 64 * sizeof(int));
+    if (e != cudaSuccess) return fail(DBCSR_ERR_ALLOC, std::string("flag buffer: ") + cudaGetErrorString(e));
     g_ctx.device = dev;
     return DBCSR_OK;
 }
@@ -600,7 +602,7 @@ int multiply_dense(bool ta, bool tb, double alpha, dbcsr_matrix_s* A, dbcsr_matr
         DB_TRY(dgemm_fp64(M, N, K, alpha, dA.p, M, dB.p, K, beta_eff, dC.p, M));
         g_stats.main_flops = 2.0 * (double)M * (double)N * (double)K;
     } else {
-        DB_TRY(dgemm_emulated(M, N, K, alpha, dA.p, M, dB.p, K, beta_eff, dC.p, M, o));
+        DB_TRY(dgemm_emulated(M, N, K, alpha, dA.p, M, dB.p, K, beta_eff, dC.p, M, o, &g_stats.main_flops));
     }
     mark(2);
     if (o.precision != DBCSR_PREC_OZAKI)

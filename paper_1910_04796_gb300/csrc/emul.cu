@@ -1,15 +1,279 @@
-// emul.cu -- emulated-precision paths (filled in by the Ozaki / TF32 kernels).
+// emul.cu -- emulated-FP64 dense product with 7-bit integer slices
+// (Ozaki, Ogita, Oishi & Rump 2012, integer form) on the tensor cores.
+//
+//   1. exponents: e_i = frexp exponent of max_l |A(i,l)|, f_j likewise for
+//      the columns of B, so |A(i,l)| 2^-e_i < 1 and |B(l,j)| 2^-f_j < 1;
+//   2. slices: sigma_t = the t-th 7-bit group of floor(|x| 2^(7s)) with the
+//      sign of x -- the same integers as s rounds of "truncate x 2^(7t),
+//      subtract", extracted here from the FP64 bit pattern with integer
+//      operations (exact, no FP64 arithmetic); stored as bf16 (exact);
+//   3. level sums G_d = sum_{t+u=d} S^A_t S^B_u for d = 2 .. s+1 on the
+//      tensor cores, exactly (tc_ozaki.cu);
+//   4. recombination in FP64: acc = sum_{d=s+1..2} G_d 2^(-7d) (one rounding
+//      per level, smallest first), C = alpha (acc 2^(e_i+f_j)) + beta C.
+// Steps 1, 2 and 4 are HBM-bound elementwise kernels; step 3 carries the work.
+#include <cuda_bf16.h>
+
 #include "emul.cuh"
+#include "tc_gemm.cuh"
 
 namespace dbcsr {
 
-int dgemm_emulated(int64_t, int64_t, int64_t, double, const double*, int64_t, const double*, int64_t, double,
-                   double*, int64_t, const dbcsr_opts&) {
-    return fail(DBCSR_ERR_ARG, "emulated precision is not available in this build");
+namespace {
+
+constexpr int OZ_KSEG_BLOCKS = 256;   // 16384: s * 16384 * 127^2 < 2^31 for s <= 8
+
+// max |A(i,l)| over l for column-major A: bit patterns of non-negative
+// doubles order like the values, so an unsigned max is a max of magnitudes.
+__global__ void k_rowmax_bits(int64_t M, int64_t K, const double* __restrict__ A, int64_t lda, int64_t kchunk,
+                              unsigned long long* __restrict__ out) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    const int64_t l0 = blockIdx.y * kchunk, l1 = min(K, l0 + kchunk);
+    unsigned long long mx = 0;
+    for (int64_t l = l0; l < l1; l++) {
+        unsigned long long b = (unsigned long long)__double_as_longlong(A[i + l * lda]) & 0x7fffffffffffffffull;
+        mx = b > mx ? b : mx;
+    }
+    if (mx) atomicMax(&out[i], mx);
+}
+
+// max |B(l,j)| over l for column-major B: one CTA per column
+__global__ void k_colmax_bits(int64_t K, const double* __restrict__ B, int64_t ldb,
+                              unsigned long long* __restrict__ out) {
+    const int64_t j = blockIdx.x;
+    unsigned long long mx = 0;
+    for (int64_t l = threadIdx.x; l < K; l += blockDim.x) {
+        unsigned long long b = (unsigned long long)__double_as_longlong(B[l + j * ldb]) & 0x7fffffffffffffffull;
+        mx = b > mx ? b : mx;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        unsigned long long y = __shfl_xor_sync(0xffffffffu, mx, o);
+        mx = y > mx ? y : mx;
+    }
+    __shared__ unsigned long long sh[32];
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); w++) mx = sh[w] > mx ? sh[w] : mx;
+        out[j] = mx;
+    }
+}
+
+__global__ void k_exponents(int64_t n, const unsigned long long* __restrict__ bits, int* __restrict__ e) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double mu = __longlong_as_double((long long)bits[i]);
+    int ex = 0;
+    if (mu != 0.0) frexp(mu, &ex);
+    e[i] = ex;
+}
+
+// floor(|x| 2^(7s - e)) with the sign of x, from the bit pattern of x.
+// |x| 2^-e < 1 guarantees the result is below 2^(7s) <= 2^56.
+__device__ __forceinline__ long long fixed_point(double x, int e, int s) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int ex = (int)((b >> 52) & 0x7ff);
+    unsigned long long m = b & 0xfffffffffffffull;
+    int E;   // |x| = m * 2^E
+    if (ex == 0) {
+        E = -1074;
+    } else {
+        m |= 1ull << 52;
+        E = ex - 1075;
+    }
+    const int sh = E - e + 7 * s;
+    unsigned long long q;
+    if (m == 0) q = 0;
+    else if (sh >= 0) q = m << sh;
+    else if (sh > -64) q = m >> (-sh);
+    else q = 0;
+    return (b >> 63) ? -(long long)q : (long long)q;
+}
+
+__device__ __forceinline__ __nv_bfloat16 slice_bf16(long long q, int t, int s) {
+    const unsigned long long a = (unsigned long long)(q < 0 ? -q : q);
+    int v = (int)((a >> (7 * (s - t))) & 127ull);
+    if (q < 0) v = -v;
+    return __float2bfloat16_rn((float)v);   // |v| <= 127: exact
+}
+
+// A (column-major M x K) -> SA[t][i][l] (row-major, ldk), zero for l >= K.
+// 32 (rows) x 64 (k) tiles through shared memory so that both sides coalesce.
+__global__ void __launch_bounds__(256) k_slice_rows(int64_t M, int64_t K, int64_t ldk, const double* __restrict__ A,
+                                                    int64_t lda, const int* __restrict__ e, int s,
+                                                    __nv_bfloat16* __restrict__ SA) {
+    __shared__ long long q[32][65];
+    const int64_t i0 = blockIdx.y * 32, l0 = blockIdx.x * 64;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+    for (int ll = ty; ll < 64; ll += 8) {
+        const int64_t i = i0 + tx, l = l0 + ll;
+        long long v = 0;
+        if (i < M && l < K) v = fixed_point(A[i + l * lda], e[i], s);
+        q[tx][ll] = v;
+    }
+    __syncthreads();
+    // write: each thread two consecutive k of one row, for every slice
+    for (int idx = threadIdx.x; idx < 32 * 32; idx += 256) {
+        const int r = idx >> 5, cp = (idx & 31) * 2;
+        const int64_t i = i0 + r;
+        if (i >= M) continue;
+        for (int t = 1; t <= s; t++) {
+            __nv_bfloat162 pr;
+            pr.x = slice_bf16(q[r][cp], t, s);
+            pr.y = slice_bf16(q[r][cp + 1], t, s);
+            *reinterpret_cast<__nv_bfloat162*>(SA + ((int64_t)(t - 1) * M + i) * ldk + l0 + cp) = pr;
+        }
+    }
+}
+
+// B (column-major K x N) -> SB[u][j][l] (ldk), zero for l >= K.
+__global__ void k_slice_cols(int64_t N, int64_t K, int64_t ldk, const double* __restrict__ B, int64_t ldb,
+                             const int* __restrict__ f, int s, __nv_bfloat16* __restrict__ SB) {
+    const int64_t j = blockIdx.y;
+    const int64_t l = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) * 2;
+    if (l >= ldk) return;
+    long long q0 = (l < K) ? fixed_point(B[l + j * ldb], f[j], s) : 0;
+    long long q1 = (l + 1 < K) ? fixed_point(B[l + 1 + j * ldb], f[j], s) : 0;
+    for (int u = 1; u <= s; u++) {
+        __nv_bfloat162 pr;
+        pr.x = slice_bf16(q0, u, s);
+        pr.y = slice_bf16(q1, u, s);
+        *reinterpret_cast<__nv_bfloat162*>(SB + ((int64_t)(u - 1) * N + j) * ldk + l) = pr;
+    }
+}
+
+// C = alpha * (sum_{d=s+1..2} G_d 2^(-7d)) 2^(e_i+f_j) + beta * C
+__global__ void k_recombine(int64_t M, int64_t N, int s, int ksegs, const double* __restrict__ ws, int64_t stride,
+                            const int* __restrict__ e, const int* __restrict__ f, double alpha, double beta,
+                            double* __restrict__ C, int64_t ldc) {
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= M * N) return;
+    const int64_t i = idx % M, j = idx / M;
+    double acc = 0.0;
+    for (int d = s + 1; d >= 2; d--) {
+        double g = 0.0;   // exact: integer partial sums below 2^53
+        for (int k = 0; k < ksegs; k++) g += ws[((int64_t)(d - 2) * ksegs + k) * stride + idx];
+        acc = fma(g, ldexp(1.0, -7 * d), acc);   // g * 2^-7d is exact: one rounding
+    }
+    double v = __dmul_rn(alpha, ldexp(acc, e[i] + f[j]));
+    if (beta != 0.0) v = __dadd_rn(v, __dmul_rn(beta, C[i + j * ldc]));
+    C[i + j * ldc] = v;
+}
+
+__global__ void k_scale_c(int64_t M, int64_t N, double beta, double* __restrict__ C, int64_t ldc) {
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= M * N) return;
+    const int64_t i = idx % M, j = idx / M;
+    C[i + j * ldc] = beta != 0.0 ? __dmul_rn(beta, C[i + j * ldc]) : 0.0;
+}
+
+}  // namespace
+
+int oz_exponents(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda, const double* B, int64_t ldb,
+                 int* e, int* f) {
+    cudaStream_t st = ctx().stream;
+    DBuf<unsigned long long> rb, cb;
+    DB_TRY(rb.alloc(M ? M : 1));
+    DB_TRY(cb.alloc(N ? N : 1));
+    DB_CUDA(cudaMemsetAsync(rb.p, 0, sizeof(unsigned long long) * (M ? M : 1), st));
+    if (M > 0 && K > 0) {
+        const int64_t kchunk = 256;
+        dim3 g((unsigned)cdiv(M, 256), (unsigned)cdiv(K, kchunk));
+        if (g.y > 65535) return fail(DBCSR_ERR_OVERFLOW, "emulated gemm: K too large");
+        k_rowmax_bits<<<g, 256, 0, st>>>(M, K, A, lda, kchunk, rb.p);
+        DB_KCHECK();
+    }
+    if (N > 0) {
+        k_colmax_bits<<<(unsigned)N, 256, 0, st>>>(K, B, ldb, cb.p);
+        DB_KCHECK();
+    }
+    if (M > 0) {
+        k_exponents<<<(unsigned)cdiv(M, 256), 256, 0, st>>>(M, rb.p, e);
+        DB_KCHECK();
+    }
+    if (N > 0) {
+        k_exponents<<<(unsigned)cdiv(N, 256), 256, 0, st>>>(N, cb.p, f);
+        DB_KCHECK();
+    }
+    return DBCSR_OK;
+}
+
+int dgemm_ozaki(int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda, const double* B,
+                int64_t ldb, double beta, double* C, int64_t ldc, int s, double* main_flops, double* main_ms_unused) {
+    (void)main_ms_unused;
+    cudaStream_t st = ctx().stream;
+    if (M == 0 || N == 0) return DBCSR_OK;
+    if (K == 0) {
+        k_scale_c<<<(unsigned)cdiv(M * N, 256), 256, 0, st>>>(M, N, beta, C, ldc);
+        DB_KCHECK();
+        return DBCSR_OK;
+    }
+    if (M >= INT32_MAX || N >= INT32_MAX) return fail(DBCSR_ERR_OVERFLOW, "emulated gemm: dimension too large");
+    const int64_t ldk = cdiv(K, 64) * 64;
+    DBuf<int> e, f;
+    DB_TRY(e.alloc(M));
+    DB_TRY(f.alloc(N));
+    DB_TRY(oz_exponents(M, N, K, A, lda, B, ldb, e.p, f.p));
+    DBuf<__nv_bfloat16> SA, SB;
+    DB_TRY(SA.alloc((size_t)s * M * ldk));
+    DB_TRY(SB.alloc((size_t)s * N * ldk));
+    {
+        dim3 g((unsigned)(ldk / 64), (unsigned)cdiv(M, 32));
+        if (g.y > 65535) return fail(DBCSR_ERR_OVERFLOW, "emulated gemm: M too large for the slicing grid");
+        k_slice_rows<<<g, 256, 0, st>>>(M, K, ldk, A, lda, e.p, s, SA.p);
+        DB_KCHECK();
+        dim3 g2((unsigned)cdiv(ldk / 2, 256), (unsigned)N);
+        if (N > 2147483647LL) return fail(DBCSR_ERR_OVERFLOW, "emulated gemm: N too large");
+        k_slice_cols<<<g2, 256, 0, st>>>(N, K, ldk, B, ldb, f.p, s, SB.p);
+        DB_KCHECK();
+    }
+    const int tn = 128;
+    CUtensorMap tmA, tmB;
+    DB_TRY(make_slice_tmap(&tmA, SA.p, ldk, M, s, 128, 2));
+    DB_TRY(make_slice_tmap(&tmB, SB.p, ldk, N, s, tn, 2));
+    OzParams p;
+    p.M = (int)M;
+    p.N = (int)N;
+    p.kblocks = (int)(ldk / 64);
+    p.s = s;
+    p.kseg_blocks = OZ_KSEG_BLOCKS;
+    p.ksegs = (int)cdiv(p.kblocks, OZ_KSEG_BLOCKS);
+    p.tiles_m = (int)cdiv(M, 128);
+    p.tiles_n = (int)cdiv(N, tn);
+    p.units = (int64_t)p.tiles_m * p.tiles_n * p.ksegs * s;
+    p.ws_stride = M * N;
+    DBuf<double> ws;
+    DB_TRY(ws.alloc((size_t)s * p.ksegs * M * N));
+    p.ws = ws.p;
+    p.err = ctx().d_flags;
+    DB_CUDA(cudaMemsetAsync(p.err, 0, sizeof(int), st));
+    DB_TRY(oz_gemm_launch(tmA, tmB, p, tn));
+    int h_err = 0;
+    DB_CUDA(cudaMemcpyAsync(&h_err, p.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    k_recombine<<<(unsigned)cdiv(M * N, 256), 256, 0, st>>>(M, N, s, p.ksegs, ws.p, p.ws_stride, e.p, f.p, alpha,
+                                                           beta, C, ldc);
+    DB_KCHECK();
+    DB_CUDA(cudaStreamSynchronize(st));
+    if (h_err) return fail(DBCSR_ERR_TIMEOUT, "emulated gemm: a tensor-core pipeline wait timed out");
+    if (main_flops) *main_flops = 2.0 * (double)(p.tiles_m * 128) * (double)(p.tiles_n * tn) * (double)ldk *
+                                  (double)(s * (s + 1) / 2);
+    return DBCSR_OK;
+}
+
+int dgemm_emulated(int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda, const double* B,
+                   int64_t ldb, double beta, double* C, int64_t ldc, const dbcsr_opts& o, double* main_flops) {
+    if (o.precision == DBCSR_PREC_OZAKI) {
+        const int s = o.ozaki_slices > 0 ? o.ozaki_slices : 7;
+        if (s > 8) return fail(DBCSR_ERR_ARG, "ozaki_slices must be 1..8");
+        return dgemm_ozaki(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s, main_flops, nullptr);
+    }
+    return fail(DBCSR_ERR_ARG, "TF32 precision is not available in this build");
 }
 
 int smm_emulated(const SmmArgs&, int, int, int, const dbcsr_opts&) {
-    return fail(DBCSR_ERR_ARG, "emulated precision is not available in this build");
+    return fail(DBCSR_ERR_ARG, "emulated precision on the stack path is not available in this build");
 }
 
 }  // namespace dbcsr

@@ -277,4 +277,4 @@ def has_precision(name: str) -> bool:
     return name in _AVAILABLE
 
 
-_AVAILABLE = {"fp64"}
+_AVAILABLE = {"fp64", "ozaki"}
