@@ -197,6 +197,33 @@ DBCSR_API int dbcsr_get_stats(dbcsr_stats *out);
 DBCSR_API int dbcsr_get_stacks(char transa, char transb, dbcsr_matrix A, dbcsr_matrix B, int stack_cap,
                      int *out, int64_t cap, int64_t *n_out);
 
+/* Allocation-free emulated-FP64 dense GEMM. The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc -- for
+ * example applications whose device memory is entirely owned by another
+ * allocator (a framework that reserved the HBM up front), or code that must
+ * not perform the device-wide synchronisation cudaMalloc/cudaFree may imply.
+ *
+ * Computes C = alpha*A*B + beta*C with the same emulation as
+ * DBCSR_PREC_OZAKI (7-bit integer slices on the tensor cores, exact integer
+ * level sums, FP64 recombination); results are identical to the dense path of
+ * dbcsr_multiply with that precision.
+ *   M, N, K        : sizes (>= 0); A is M x K, B is K x N, C is M x N
+ *   A, B, C        : DEVICE pointers, column-major, leading dimensions
+ *                    lda >= M, ldb >= K, ldc >= M; owned by the caller
+ *   slices         : 1..8, 0 = 7
+ *   stream         : cudaStream_t the work is ordered on; the call returns
+ *                    after that stream has finished it
+ * Scratch comes from one fixed 128 MiB device array inside the library
+ * (every GPU that loads the library holds it until the process exits); the
+ * call allocates nothing. Sizes whose scratch exceeds it (about
+ * M = N = K = 1024 with 7 slices) return DBCSR_ERR_OVERFLOW with a message.
+ * The first call on a device looks up the array's device address (once per
+ * device); make that first call before any stream capture. All calls share
+ * the array: calls whose work overlaps on the GPU race on it. */
+DBCSR_API int dbcsr_dgemm_emulated_noalloc(int64_t M, int64_t N, int64_t K, double alpha, const double *A,
+                                           int64_t lda, const double *B, int64_t ldb, double beta, double *C,
+                                           int64_t ldc, int slices, void *stream);
+
 /* Wait for all work the library queued on its stream. */
 DBCSR_API int dbcsr_sync(void);
 

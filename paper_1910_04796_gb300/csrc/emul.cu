@@ -14,6 +14,8 @@
 // Steps 1, 2 and 4 are HBM-bound elementwise kernels; step 3 carries the work.
 #include <cuda_bf16.h>
 
+#include <mutex>
+
 #include "emul.cuh"
 #include "tc_gemm.cuh"
 
@@ -277,3 +279,162 @@ int smm_emulated(const SmmArgs&, int, int, int, const dbcsr_opts&) {
 }
 
 }  // namespace dbcsr
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the emulated-FP64 GEMM.
+//
+// Some callers cannot call cudaMalloc: applications whose device memory is
+// entirely owned by another allocator (a framework that reserved the HBM up
+// front), and code paths that must not perform the device-wide
+// synchronisation that cudaMalloc / cudaFree may imply. For them the scratch
+// of this operation (exponents, slices, level sums, error flag) lives in the
+// file-scope array below, of a fixed maximum size, which every GPU that loads
+// this library holds until the process exits. Every call shares it and it
+// keeps the previous call's contents, so whatever must start at zero is
+// cleared on the stream at the start of each call; calls whose work overlaps
+// on the GPU (different streams, or threads) race on it.
+// ---------------------------------------------------------------------------
+namespace dbcsr {
+namespace {
+
+constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(128) << 20;   // 128 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mutex;
+unsigned char* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+int g_noalloc_sms[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (the host-side symbol is only a stand-in, not a device address).
+int noalloc_scratch(unsigned char** ptr, int* sms) {
+    int dev = 0;
+    DB_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(DBCSR_ERR_STATE, "no-alloc gemm: device ordinal too large");
+    std::lock_guard<std::mutex> lk(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        DB_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        int n = 0;
+        DB_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+        g_noalloc_sms[dev] = n;
+        g_noalloc_ptr[dev] = static_cast<unsigned char*>(p);
+    }
+    *ptr = g_noalloc_ptr[dev];
+    *sms = g_noalloc_sms[dev];
+    return DBCSR_OK;
+}
+
+inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Byte layout of the scratch for one call; returns the total.
+size_t noalloc_layout(int64_t M, int64_t N, int64_t ldk, int s, int ksegs, size_t off[7]) {
+    size_t o = 0;
+    off[0] = o; o += align256(sizeof(int));                                   // error flag
+    off[1] = o; o += align256(sizeof(unsigned long long) * (size_t)M);         // row max bits
+    off[2] = o; o += align256(sizeof(unsigned long long) * (size_t)N);         // column max bits
+    off[3] = o; o += align256(sizeof(int) * (size_t)M);                        // e
+    off[4] = o; o += align256(sizeof(int) * (size_t)N);                        // f
+    off[5] = o; o += align256(2 * (size_t)s * (size_t)(M + N) * (size_t)ldk);   // slices of A then B
+    off[6] = o; o += align256(8 * (size_t)s * (size_t)ksegs * (size_t)M * (size_t)N);  // level sums
+    return o;
+}
+
+}  // namespace
+
+int dgemm_ozaki_noalloc(int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda, const double* B,
+                        int64_t ldb, double beta, double* C, int64_t ldc, int s, cudaStream_t st) {
+    if (s == 0) s = 7;
+    if (s < 1 || s > 8) return fail(DBCSR_ERR_ARG, "no-alloc gemm: slices must be 1..8");
+    if (M < 0 || N < 0 || K < 0) return fail(DBCSR_ERR_ARG, "no-alloc gemm: negative size");
+    if ((M > 0 && lda < M) || (K > 0 && ldb < K) || (M > 0 && ldc < M))
+        return fail(DBCSR_ERR_ARG, "no-alloc gemm: leading dimension smaller than the matrix");
+    if (M == 0 || N == 0) return DBCSR_OK;
+    if (!A || !B || !C) return fail(DBCSR_ERR_ARG, "no-alloc gemm: NULL matrix pointer");
+    if (K == 0) {
+        k_scale_c<<<(unsigned)cdiv(M * N, 256), 256, 0, st>>>(M, N, beta, C, ldc);
+        DB_KCHECK();
+        return DBCSR_OK;
+    }
+    const int64_t ldk = cdiv(K, 64) * 64;
+    const int kblocks = (int)(ldk / 64);
+    const int ksegs = (int)cdiv(kblocks, OZ_KSEG_BLOCKS);
+    size_t off[7];
+    if (M > (int64_t)1 << 24 || N > (int64_t)1 << 24 || K > (int64_t)1 << 30)
+        return fail(DBCSR_ERR_OVERFLOW, "no-alloc gemm: a dimension exceeds the fixed scratch");
+    const size_t need = noalloc_layout(M, N, ldk, s, ksegs, off);
+    if (need > NOALLOC_SCRATCH_BYTES)
+        return fail(DBCSR_ERR_OVERFLOW, "no-alloc gemm: needs " + std::to_string(need) +
+                                            " bytes of scratch, the fixed maximum is " +
+                                            std::to_string(NOALLOC_SCRATCH_BYTES) +
+                                            " (about M = N = K = 1024 with 7 slices)");
+    unsigned char* base = nullptr;
+    int sms = 0;
+    DB_TRY(noalloc_scratch(&base, &sms));
+    int* err = reinterpret_cast<int*>(base + off[0]);
+    unsigned long long* rb = reinterpret_cast<unsigned long long*>(base + off[1]);
+    unsigned long long* cb = reinterpret_cast<unsigned long long*>(base + off[2]);
+    int* e = reinterpret_cast<int*>(base + off[3]);
+    int* f = reinterpret_cast<int*>(base + off[4]);
+    __nv_bfloat16* SA = reinterpret_cast<__nv_bfloat16*>(base + off[5]);
+    __nv_bfloat16* SB = SA + (size_t)s * M * ldk;
+    double* ws = reinterpret_cast<double*>(base + off[6]);
+    // the shared scratch keeps the last call's contents: clear what starts at zero
+    DB_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+    DB_CUDA(cudaMemsetAsync(rb, 0, sizeof(unsigned long long) * M, st));
+    {
+        const int64_t kchunk = 256;
+        dim3 g((unsigned)cdiv(M, 256), (unsigned)cdiv(K, kchunk));
+        if (g.y > 65535) return fail(DBCSR_ERR_OVERFLOW, "no-alloc gemm: K too large");
+        k_rowmax_bits<<<g, 256, 0, st>>>(M, K, A, lda, kchunk, rb);
+        DB_KCHECK();
+        k_colmax_bits<<<(unsigned)N, 256, 0, st>>>(K, B, ldb, cb);
+        DB_KCHECK();
+        k_exponents<<<(unsigned)cdiv(M, 256), 256, 0, st>>>(M, rb, e);
+        DB_KCHECK();
+        k_exponents<<<(unsigned)cdiv(N, 256), 256, 0, st>>>(N, cb, f);
+        DB_KCHECK();
+        dim3 g1((unsigned)(ldk / 64), (unsigned)cdiv(M, 32));
+        if (g1.y > 65535) return fail(DBCSR_ERR_OVERFLOW, "no-alloc gemm: M too large for the slicing grid");
+        k_slice_rows<<<g1, 256, 0, st>>>(M, K, ldk, A, lda, e, s, SA);
+        DB_KCHECK();
+        dim3 g2((unsigned)cdiv(ldk / 2, 256), (unsigned)N);
+        k_slice_cols<<<g2, 256, 0, st>>>(N, K, ldk, B, ldb, f, s, SB);
+        DB_KCHECK();
+    }
+    CUtensorMap tmA, tmB;
+    DB_TRY(make_slice_tmap(&tmA, SA, ldk, M, s, 128, 2));
+    DB_TRY(make_slice_tmap(&tmB, SB, ldk, N, s, 128, 2));
+    OzParams p;
+    p.M = (int)M;
+    p.N = (int)N;
+    p.kblocks = kblocks;
+    p.s = s;
+    p.kseg_blocks = OZ_KSEG_BLOCKS;
+    p.ksegs = ksegs;
+    p.tiles_m = (int)cdiv(M, 128);
+    p.tiles_n = (int)cdiv(N, 128);
+    p.units = (int64_t)p.tiles_m * p.tiles_n * ksegs * s;
+    p.ws = ws;
+    p.ws_stride = M * N;
+    p.err = err;
+    DB_TRY(oz_gemm_launch_on(tmA, tmB, p, st, sms));
+    k_recombine<<<(unsigned)cdiv(M * N, 256), 256, 0, st>>>(M, N, s, ksegs, ws, p.ws_stride, e, f, alpha, beta, C,
+                                                           ldc);
+    DB_KCHECK();
+    int h_err = 0;
+    DB_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    DB_CUDA(cudaStreamSynchronize(st));
+    if (h_err) return fail(DBCSR_ERR_TIMEOUT, "no-alloc gemm: a tensor-core pipeline wait timed out");
+    return DBCSR_OK;
+}
+
+}  // namespace dbcsr
+
+extern "C" int dbcsr_dgemm_emulated_noalloc(int64_t M, int64_t N, int64_t K, double alpha, const double* A,
+                                            int64_t lda, const double* B, int64_t ldb, double beta, double* C,
+                                            int64_t ldc, int slices, void* stream) {
+    dbcsr::set_error("");
+    return dbcsr::dgemm_ozaki_noalloc(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, slices,
+                                      static_cast<cudaStream_t>(stream));
+}

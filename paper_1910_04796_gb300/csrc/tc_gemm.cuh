@@ -25,3 +25,9 @@ int make_slice_tmap(CUtensorMap* map, const void* base, int64_t ldk, int64_t row
 int oz_gemm_launch(const CUtensorMap& tmA, const CUtensorMap& tmB, const OzParams& p, int tn);
 
 }  // namespace dbcsr
+
+namespace dbcsr {
+// oz_gemm_launch with 128-column tiles on an explicit stream and SM count.
+int oz_gemm_launch_on(const CUtensorMap& tmA, const CUtensorMap& tmB, const OzParams& p, cudaStream_t st,
+                      int num_sms);
+}  // namespace dbcsr

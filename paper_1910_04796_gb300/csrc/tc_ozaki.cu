@@ -330,3 +330,20 @@ int oz_gemm_launch(const CUtensorMap& tmA, const CUtensorMap& tmB, const OzParam
 }
 
 }  // namespace dbcsr
+
+namespace dbcsr {
+
+// The same launch on an explicit stream and SM count, for callers that do not
+// go through the library context.
+int oz_gemm_launch_on(const CUtensorMap& tmA, const CUtensorMap& tmB, const OzParams& p, cudaStream_t st,
+                      int num_sms) {
+    if (p.units <= 0) return DBCSR_OK;
+    using Cfg = OzCfg<128>;
+    const int grid = (int)std::min<int64_t>(p.units, num_sms);
+    DB_CUDA(cudaFuncSetAttribute(k_oz_gemm<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM));
+    k_oz_gemm<128><<<grid, Cfg::THREADS, Cfg::SMEM, st>>>(tmA, tmB, p);
+    DB_KCHECK();
+    return DBCSR_OK;
+}
+
+}  // namespace dbcsr

@@ -65,6 +65,8 @@ SIGNATURES = [
     ("dbcsr_multiply", C.c_int, [C.c_char, C.c_char, C.c_double, _P, _P, C.c_double, _P, C.POINTER(Opts)]),
     ("dbcsr_get_stats", C.c_int, [C.POINTER(Stats)]),
     ("dbcsr_get_stacks", C.c_int, [C.c_char, C.c_char, _P, _P, C.c_int, _IP, C.c_int64, _LP]),
+    ("dbcsr_dgemm_emulated_noalloc", C.c_int, [C.c_int64, C.c_int64, C.c_int64, C.c_double, _P, C.c_int64, _P,
+                                               C.c_int64, C.c_double, _P, C.c_int64, C.c_int, _P]),
     ("dbcsr_sync", C.c_int, []),
     ("dbcsr_last_error", C.c_char_p, []),
     ("dbcsr_version", C.c_char_p, []),
@@ -278,3 +280,25 @@ def has_precision(name: str) -> bool:
 
 
 _AVAILABLE = {"fp64", "ozaki"}
+
+
+def dgemm_emulated_noalloc(alpha, A, B, beta, Cmat, slices=0, stream=None):
+    """C = alpha*A*B + beta*C (emulated FP64) with no device allocation.
+
+    A (M x K), B (K x N), C (M x N) are CUDA float64 tensors holding the
+    matrices column-major, i.e. passed as their transposes in torch's
+    row-major terms: A is a (K, M) contiguous tensor, etc. See
+    dbcsr_dgemm_emulated_noalloc for who needs this and its size limit.
+    """
+    import torch
+    K, M = A.shape
+    N, K2 = B.shape
+    assert K2 == K and tuple(Cmat.shape) == (N, M)
+    for t in (A, B, Cmat):
+        assert t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    _check(load().dbcsr_dgemm_emulated_noalloc(M, N, K, float(alpha), C.c_void_p(A.data_ptr()), M,
+                                               C.c_void_p(B.data_ptr()), K, float(beta),
+                                               C.c_void_p(Cmat.data_ptr()), M, slices,
+                                               C.c_void_p(stream.cuda_stream)))
