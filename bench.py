@@ -291,7 +291,7 @@ def main():
     for _ in range(max(1, min(3, args.steps))):
         step(timing=True)
         s2 = dbcsr.stats()
-        mains.append(s2["ms_main"])
+        mains.append(s2["ms_kernel"])
         totals.append(s2["ms_total"])
     main_ms = statistics.median(mains)
     s2 = dbcsr.stats()

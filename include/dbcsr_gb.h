@@ -108,6 +108,8 @@ typedef struct {
     double main_flops;       /* arithmetic the main kernels executed (2*M*N*K per
                                 GEMM issued, incl. slices / padding)             */
     double main_bytes;       /* algorithmic HBM bytes of the main kernels         */
+    float ms_kernel;         /* the dominant kernel alone (GEMM / batched SMM)    */
+    float reserved_f;
 } dbcsr_stats;
 
 /* Select the stream (a cudaStream_t, may be NULL for the legacy default

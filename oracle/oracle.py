@@ -281,3 +281,18 @@ def ozaki_gemm(alpha, Ad, Bd, beta, Cd, s=7, rows=None, nthreads=0, want_levels=
     if rc != 0:
         raise ValueError("oracle_ozaki_gemm failed")
     return Cd, lv
+
+
+# --------------------------------------------------------------------------
+# TF32 variant: inputs rounded FP64 -> FP32 (nearest even) -> TF32 (10-bit
+# mantissa, nearest with ties away from zero); products and sums in FP32.
+# --------------------------------------------------------------------------
+def round_tf32(x) -> np.ndarray:
+    """FP64 values rounded to TF32 (returned as FP64, exactly representable)."""
+    f = np.asarray(x, np.float64).astype(np.float32)
+    b = f.view(np.uint32).copy()
+    mag = b & np.uint32(0x7FFFFFFF)
+    finite = mag < np.uint32(0x7F800000)
+    r = (mag + np.uint32(0x1000)) & np.uint32(0xFFFFE000)
+    b = np.where(finite, (b & np.uint32(0x80000000)) | r, b)
+    return b.view(np.float32).astype(np.float64)

@@ -418,7 +418,8 @@ namespace {
 // CUDA events on the library stream around the phases of one multiply
 struct PhaseTimer {
     bool on = false;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool kernel_marked = false;
+    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     void init(bool enable) {
         on = enable;
         if (!on) return;
@@ -427,6 +428,7 @@ struct PhaseTimer {
     }
     void mark(int i) {
         if (on) cudaEventRecord(ev[i], g_ctx.stream);
+        if (on && i == 5) kernel_marked = true;
     }
     void finish(dbcsr_stats& s) {
         if (!on) return;
@@ -435,6 +437,8 @@ struct PhaseTimer {
         cudaEventElapsedTime(&s.ms_main, ev[1], ev[2]);
         cudaEventElapsedTime(&s.ms_finish, ev[2], ev[3]);
         cudaEventElapsedTime(&s.ms_total, ev[0], ev[3]);
+        if (kernel_marked) cudaEventElapsedTime(&s.ms_kernel, ev[4], ev[5]);
+        else s.ms_kernel = s.ms_main;
     }
     ~PhaseTimer() {
         for (auto& e : ev)
@@ -445,6 +449,14 @@ PhaseTimer* g_timer = nullptr;
 inline void mark(int i) {
     if (g_timer) g_timer->mark(i);
 }
+
+}  // namespace
+
+// around the dominant kernel of a multiply (events 4 and 5 of the phase timer)
+void timer_kernel_begin() { mark(4); }
+void timer_kernel_end() { mark(5); }
+
+namespace {
 
 int check_conformant(bool ta, bool tb, dbcsr_matrix_s* A, dbcsr_matrix_s* B, dbcsr_matrix_s* C) {
     const std::vector<int>& a_rows = ta ? A->h_cs : A->h_rs;
@@ -535,7 +547,11 @@ int multiply_stacks(bool ta, bool tb, double alpha, dbcsr_matrix_s* A, dbcsr_mat
         rc = smm_fp64_generic(g, C->max_rs * C->max_cs);
         g_stats.main_flops = g_stats.useful_flops;
     } else {
-        rc = smm_emulated(g, C->max_rs, C->max_cs, std::max(A->max_rs, A->max_cs), o);
+        rc = smm_emulated(g, A, ta, B, tb, C, o, nullptr);
+        const int s = o.ozaki_slices > 0 ? o.ozaki_slices : 7;
+        auto r16 = [](int x) { return (double)((x + 15) & ~15); };
+        g_stats.main_flops = (double)P.nprod * (s * (s + 1) / 2) * 2.0 * r16(C->max_rs) * r16(C->max_cs) *
+                             r16(ta ? A->max_rs : A->max_cs);
     }
     mark(2);
     if (rc) { dfree(data, (size_t)(P.nelem ? P.nelem : 1)); return rc; }

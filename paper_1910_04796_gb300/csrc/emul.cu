@@ -24,6 +24,7 @@ namespace dbcsr {
 namespace {
 
 constexpr int OZ_KSEG_BLOCKS = 256;   // 16384: s * 16384 * 127^2 < 2^31 for s <= 8
+constexpr int OZ_CHUNK_BLOCKS = 16;   // 1024: 1024 * 127^2 < 2^24, exact in fp32
 
 // max |A(i,l)| over l for column-major A: bit patterns of non-negative
 // doubles order like the values, so an unsigned max is a max of magnitudes.
@@ -235,7 +236,9 @@ int dgemm_ozaki(int64_t M, int64_t N, int64_t K, double alpha, const double* A, 
     CUtensorMap tmA, tmB;
     DB_TRY(make_slice_tmap(&tmA, SA.p, ldk, M, s, 128, 2));
     DB_TRY(make_slice_tmap(&tmB, SB.p, ldk, N, s, tn, 2));
-    OzParams p;
+    OzParams p{};
+    p.chunk_blocks = OZ_CHUNK_BLOCKS;
+    p.elem_bytes = 2;
     p.M = (int)M;
     p.N = (int)N;
     p.kblocks = (int)(ldk / 64);
@@ -251,7 +254,9 @@ int dgemm_ozaki(int64_t M, int64_t N, int64_t K, double alpha, const double* A, 
     p.ws = ws.p;
     p.err = ctx().d_flags;
     DB_CUDA(cudaMemsetAsync(p.err, 0, sizeof(int), st));
+    timer_kernel_begin();
     DB_TRY(oz_gemm_launch(tmA, tmB, p, tn));
+    timer_kernel_end();
     int h_err = 0;
     DB_CUDA(cudaMemcpyAsync(&h_err, p.err, sizeof(int), cudaMemcpyDeviceToHost, st));
     k_recombine<<<(unsigned)cdiv(M * N, 256), 256, 0, st>>>(M, N, s, p.ksegs, ws.p, p.ws_stride, e.p, f.p, alpha,
@@ -271,12 +276,10 @@ int dgemm_emulated(int64_t M, int64_t N, int64_t K, double alpha, const double* 
         if (s > 8) return fail(DBCSR_ERR_ARG, "ozaki_slices must be 1..8");
         return dgemm_ozaki(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, s, main_flops, nullptr);
     }
-    return fail(DBCSR_ERR_ARG, "TF32 precision is not available in this build");
+    if (o.precision == DBCSR_PREC_TF32) return dgemm_tf32(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, main_flops);
+    return fail(DBCSR_ERR_ARG, "unknown precision");
 }
 
-int smm_emulated(const SmmArgs&, int, int, int, const dbcsr_opts&) {
-    return fail(DBCSR_ERR_ARG, "emulated precision on the stack path is not available in this build");
-}
 
 }  // namespace dbcsr
 
@@ -405,7 +408,9 @@ int dgemm_ozaki_noalloc(int64_t M, int64_t N, int64_t K, double alpha, const dou
     CUtensorMap tmA, tmB;
     DB_TRY(make_slice_tmap(&tmA, SA, ldk, M, s, 128, 2));
     DB_TRY(make_slice_tmap(&tmB, SB, ldk, N, s, 128, 2));
-    OzParams p;
+    OzParams p{};
+    p.chunk_blocks = OZ_CHUNK_BLOCKS;
+    p.elem_bytes = 2;
     p.M = (int)M;
     p.N = (int)N;
     p.kblocks = kblocks;

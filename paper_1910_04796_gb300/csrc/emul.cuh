@@ -11,7 +11,14 @@ namespace dbcsr {
 int dgemm_emulated(int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda, const double* B,
                    int64_t ldb, double beta, double* C, int64_t ldc, const dbcsr_opts& o, double* main_flops);
 
-// Stack path in emulated precision (same contract as smm_fp64_generic).
-int smm_emulated(const SmmArgs& g, int max_m, int max_n, int max_k, const dbcsr_opts& o);
+// TF32 variant of the dense GEMM (tf32.cu).
+int dgemm_tf32(int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda, const double* B,
+               int64_t ldb, double beta, double* C, int64_t ldc, double* main_flops);
+
+// Stack path in emulated FP64 (same contract as smm_fp64_generic); A, B are
+// the stored operands (op() given by ta, tb), C the result matrix whose sizes
+// and offsets describe the new blocks. Blocks up to 32 x 32.
+int smm_emulated(const SmmArgs& g, dbcsr_matrix_s* A, bool ta, dbcsr_matrix_s* B, bool tb, dbcsr_matrix_s* C,
+                 const dbcsr_opts& o, double* main_flops);
 
 }  // namespace dbcsr

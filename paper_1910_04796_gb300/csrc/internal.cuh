@@ -34,6 +34,9 @@ int fail(int code, const std::string& msg);
 
 // after every kernel launch: count it and surface launch errors
 void count_launch();
+// CUDA events around the dominant kernel of a multiply (no-ops unless timing)
+void timer_kernel_begin();
+void timer_kernel_end();
 #define DB_KCHECK()                 \
     do {                            \
         ::dbcsr::count_launch();    \

@@ -6,28 +6,33 @@
 
 namespace dbcsr {
 
-// Integer-slice GEMM of the emulated-FP64 product.
+// Work description of one tcgen05 GEMM launch (see tc_ozaki.cu).
 struct OzParams {
     int M, N;             // output size
-    int kblocks;          // ldk / 64
-    int s;                // slices per operand
+    int kblocks;          // K blocks of 128 bytes (64 bf16 / 32 fp32)
+    int s;                // levels d = 2 .. s+1 (slices per operand; 1 for TF32)
     int ksegs;            // K segments (exact int32 accumulation per segment)
     int kseg_blocks;      // k-blocks per segment
+    int chunk_blocks;     // k-blocks accumulated in TMEM before the epilogue takes them
+    int elem_bytes;       // 2 (bf16 slices) or 4 (tf32)
     int tiles_m, tiles_n;
-    int64_t units;        // tiles_m * tiles_n * ksegs * s (levels d = 2 .. s+1)
-    double* ws;           // [s][ksegs][N][M] exact level sums (column-major M x N)
+    int64_t units;        // tiles_m * tiles_n * ksegs * s
+    double* ws;           // slices: [s][ksegs][N][M] exact level sums (column-major M x N)
     int64_t ws_stride;    // M * N
+    double* C;            // tf32: output, column-major
+    int64_t ldc;
+    double alpha, beta;
     int* err;             // set to 1 on a timed-out wait
 };
 
 int make_slice_tmap(CUtensorMap* map, const void* base, int64_t ldk, int64_t rows, int slices, int box_rows,
                     int elem_bytes);
+// slice GEMMs (bf16, 128 x 128 tiles) on the library stream
 int oz_gemm_launch(const CUtensorMap& tmA, const CUtensorMap& tmB, const OzParams& p, int tn);
-
-}  // namespace dbcsr
-
-namespace dbcsr {
-// oz_gemm_launch with 128-column tiles on an explicit stream and SM count.
+// the same on an explicit stream and SM count
 int oz_gemm_launch_on(const CUtensorMap& tmA, const CUtensorMap& tmB, const OzParams& p, cudaStream_t st,
                       int num_sms);
+// TF32 GEMM writing C directly
+int tf32_gemm_launch(const CUtensorMap& tmA, const CUtensorMap& tmB, const OzParams& p);
+
 }  // namespace dbcsr

@@ -38,7 +38,8 @@ class Stats(C.Structure):
                 ("c_blocks", C.c_int64), ("useful_flops", C.c_double), ("path", C.c_int),
                 ("precision", C.c_int), ("kernel_launches", C.c_int), ("reserved", C.c_int),
                 ("ms_setup", C.c_float), ("ms_main", C.c_float), ("ms_finish", C.c_float),
-                ("ms_total", C.c_float), ("main_flops", C.c_double), ("main_bytes", C.c_double)]
+                ("ms_total", C.c_float), ("main_flops", C.c_double), ("main_bytes", C.c_double),
+                ("ms_kernel", C.c_float), ("reserved_f", C.c_float)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -279,7 +280,7 @@ def has_precision(name: str) -> bool:
     return name in _AVAILABLE
 
 
-_AVAILABLE = {"fp64", "ozaki"}
+_AVAILABLE = {"fp64", "ozaki", "tf32"}
 
 
 def dgemm_emulated_noalloc(alpha, A, B, beta, Cmat, slices=0, stream=None):

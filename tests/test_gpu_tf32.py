@@ -1,0 +1,46 @@
+"""GPU check of the TF32 variant (inputs rounded to TF32, FP32 accumulation).
+
+Its error against FP64 is reported, not bounded by the method; what is pinned
+is the input rounding: the GPU result must agree with the exact product of the
+TF32-rounded inputs to FP32-accumulation accuracy, and lie within a sanity
+band of the FP64 result.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1910_04796_gb300 import dbcsr, synth
+
+from gpu_util import gpu_multiply, assert_same_pattern
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("nb,nk,bs", [(6, 5, 22), (9, 9, 32), (3, 17, 13)])
+def test_tf32_matches_rounded_inputs(nb, nk, bs):
+    rng = np.random.default_rng(500 + nb)
+    A = synth.dense_matrix(rng, nb, nk, bs, bs)
+    B = synth.dense_matrix(rng, nk, nb + 1, bs, bs)
+    Cm = synth.dense_matrix(rng, nb, nb + 1, bs, bs)
+    got, st = gpu_multiply("N", "N", 1.0, A, B, 0.5, Cm, path="dense", precision="tf32")
+    assert st["precision"] == dbcsr.PREC_TF32
+    Ad, Bd, Cd = O.densify(A), O.densify(B), O.densify(Cm)
+    exact_rounded = O.round_tf32(Ad) @ O.round_tf32(Bd) + 0.5 * Cd
+    g = O.densify(got)
+    e_round = O.normwise_error(g, exact_rounded, Ad, Bd)
+    e_fp64 = O.normwise_error(g, Ad @ Bd + 0.5 * Cd, Ad, Bd)
+    assert e_round <= 2e-6, e_round
+    assert e_fp64 < 1e-2, e_fp64
+    ref = O.multiply("N", "N", 1.0, A, B, 0.5, Cm)
+    assert_same_pattern(got, ref)
+
+
+def test_tf32_transposes_and_ragged():
+    rng = np.random.default_rng(510)
+    A = synth.dense_matrix(rng, 7, 3, 13, 5)       # K = 15: not a multiple of 32
+    B = synth.dense_matrix(rng, 3, 11, 5, 13)
+    got, _ = gpu_multiply("T", "T", 2.0, synth.transpose_blocks(A), synth.transpose_blocks(B), 0.0,
+                          path="dense", precision="tf32")
+    Ad, Bd = O.densify(A), O.densify(B)
+    e = O.normwise_error(O.densify(got), 2.0 * (O.round_tf32(Ad) @ O.round_tf32(Bd)), Ad, Bd)
+    assert e <= 2e-6

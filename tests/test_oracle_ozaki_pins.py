@@ -125,3 +125,19 @@ def test_alpha_beta_and_row_subset():
     O.ozaki_gemm(0.5, A, B, 2.0, sub, s=6, rows=[1, 4])
     assert np.array_equal(sub[[1, 4]], full[[1, 4]])
     assert np.array_equal(np.delete(sub, [1, 4], 0), np.delete(C0, [1, 4], 0))
+
+
+def test_round_tf32_known_values():
+    # TF32 keeps 10 mantissa bits: ulp(1) = 2^-10; 2^-11 is a tie, rounded away from zero
+    assert O.round_tf32([1.0 + 2.0 ** -11])[0] == 1.0 + 2.0 ** -10
+    assert O.round_tf32([-(1.0 + 2.0 ** -11)])[0] == -(1.0 + 2.0 ** -10)
+    assert O.round_tf32([1.0 + 2.0 ** -12])[0] == 1.0
+    assert O.round_tf32([1.0 + 3 * 2.0 ** -12])[0] == 1.0 + 2.0 ** -10
+    assert O.round_tf32([0.0])[0] == 0.0
+    rng = np.random.default_rng(56)
+    x = rng.uniform(-1, 1, 1000)
+    r = O.round_tf32(x)
+    assert np.all(np.abs(r - x) <= np.abs(x) * 2.0 ** -11 * 1.0001)
+    # the result has at most 11 significant bits
+    m, _ = np.frexp(r)
+    assert np.all(m * 2 ** 11 == np.round(m * 2 ** 11))
