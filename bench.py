@@ -146,13 +146,20 @@ def barrier(world):
 
 
 def max_over_ranks(x, world):
+    """Largest value over the ranks (timings: the job ends with its slowest rank)."""
     if world <= 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def aggregate_value(useful_flops_per_step, world, steps, seconds):
+    """Whole-job TFLOP/s: every rank ran `steps` steps of the same workload (replicas)."""
+    return useful_flops_per_step * world * steps / seconds / 1e12
 
 
 def cpu_oracle_sample(w, rows, threads=0):
@@ -258,6 +265,8 @@ def main():
     torch.cuda.set_device(local)
     dbcsr.init()
     pk, pk_kind = peaks()
+    from paper_1910_04796_gb300 import autotune
+    tuned = autotune.load_table()   # per-shape FP64 stack-kernel choice, if tuned on this GPU type
     w = workload(args.workload, args.scale)
     precision = args.precision
     if precision == "auto":
@@ -285,7 +294,7 @@ def main():
         secs, wall = time_steps(step, args.steps, max(args.warmup, 3) - 1, world)
     launches = dbcsr.stats()["kernel_launches"] * args.steps
     secs = max_over_ranks(secs, world)
-    value = useful * world * args.steps / secs / 1e12
+    value = aggregate_value(useful, world, args.steps, secs)
     # live timing of the dominant kernel (CUDA events on the library stream)
     mains, totals = [], []
     for _ in range(max(1, min(3, args.steps))):
@@ -315,18 +324,42 @@ def main():
                 "traffic": None, "kernel_ms": main_ms, "algorithmic_flops": s2["main_flops"],
                 "peak_source": peak_note}
 
-    # plain FP64 comparison legs (same GPU, same inputs)
-    legs = {}
+    # comparison legs on the same GPU and inputs: the plain FP64 paths, the
+    # emulated and TF32 paths with their error against the GPU FP64 result
+    legs, accuracy = {}, {}
     if not args.no_legs and rank == 0:
-        for name, prec, path in (("fp64_dense", "fp64", "dense"), ("fp64_stacks", "fp64", "stacks")):
-            if prec == precision and path == path_taken:
-                legs[name] = value / world
-                continue
+        dense_ok = w.A.nblks == len(w.A.row_sizes) * len(w.A.col_sizes)
+        combos = [("fp64_stacks", "fp64", "stacks"), ("ozaki_stacks", "ozaki", "stacks")]
+        if dense_ok:
+            combos = [("fp64_dense", "fp64", "dense"), ("ozaki_dense", "ozaki", "dense"),
+                      ("tf32_dense", "tf32", "dense")] + combos
+        ref_c = None
+        for name, prec, path in combos:
             try:
-                s_leg, _ = time_steps(lambda: step(prec, path), 1, 1, 1)
-                legs[name] = useful / s_leg / 1e12
+                Cl = dbcsr.Matrix.from_blocks(C0) if C0 is not None else dbcsr.Matrix.create(
+                    rs, cs, np.zeros(0, np.int32), np.zeros(0, np.int32))
+                dbcsr.multiply(w.transa, w.transb, w.alpha, A, B, w.beta, Cl, path=path, precision=prec,
+                               timing=True)
+                legs[name] = useful / (dbcsr.stats()["ms_total"] / 1e3) / 1e12
+                out = Cl.data_device()
+                if prec == "fp64" and ref_c is None:
+                    ref_c = out
+                elif ref_c is not None and out.numel() == ref_c.numel():
+                    nA = float(torch.linalg.vector_norm(A.data_device()))
+                    nB = float(torch.linalg.vector_norm(B.data_device()))
+                    accuracy[name + "_vs_fp64"] = float(torch.linalg.vector_norm(out - ref_c)) / (nA * nB)
+                Cl.release()
             except Exception as e:  # report, do not hide
                 legs[name] = f"error: {e}"
+        if args.workload == "small-sparse":
+            # the kept plan + CUDA graph replay of the same multiply (latency-bound case)
+            Cl = dbcsr.Matrix.create(rs, cs, np.zeros(0, np.int32), np.zeros(0, np.int32))
+            dbcsr.multiply("N", "N", 1.0, A, B, 0.0, Cl, path="stacks", reuse_plan=True)
+            s_rep, _ = time_steps(lambda: dbcsr.multiply("N", "N", 1.0, A, B, 0.0, Cl, path="stacks",
+                                                         reuse_plan=True), 50, 3, 1)
+            legs["fp64_stacks_graph_replay"] = useful * 50 / s_rep / 1e12
+            legs["graph_replay_us_per_multiply"] = s_rep / 50 * 1e6
+            Cl.release()
 
     # end to end through the C ABI with host buffers (H2D of inputs and D2H of C inside)
     e2e = None
@@ -381,7 +414,8 @@ def main():
                        "l2": "inputs larger than L2 (no flush)" if useful > 1e9 else "inputs in L2",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-            "clocks": clk.summary(), "legs_tflops": legs, "wall_s": wall,
+            "clocks": clk.summary(), "legs_tflops": legs, "accuracy_normwise": accuracy,
+            "tuned_table": tuned, "wall_s": wall,
         }
         print(json.dumps(line), flush=True)
     return 0

@@ -83,10 +83,22 @@ typedef struct {
     int path;          /* DBCSR_PATH_*                                        */
     int precision;     /* DBCSR_PREC_*                                        */
     int ozaki_slices;  /* slices per operand for DBCSR_PREC_OZAKI; 0 = default (7) */
-    int kernel;        /* stack-kernel choice: 0 = autotuned table, 1 = generic */
+    int kernel;        /* FP64 stack kernel: 0 = per-shape table set with
+                          dbcsr_set_tuning (variant 0 for untuned shapes);
+                          v = 1..4 forces variant v-1 for every block:
+                          0: one warp per C block, 256-thread CTAs;
+                          1: one warp per C block, 128-thread CTAs;
+                          2: two warps per C block (products split);
+                          3: four warps per C block                     */
     int timing;        /* nonzero: time the phases with CUDA events on the
                           library stream (reported by dbcsr_get_stats)        */
-    int reserved[3];   /* must be zero                                        */
+    int reuse_plan;    /* nonzero (FP64 stack path): keep this multiply's stack
+                          plan with C and capture its product kernel in a CUDA
+                          graph; a later multiply of the same A and B handles
+                          (patterns unchanged, values may change), same op(),
+                          alpha and beta, into the C it produced, skips stack
+                          generation and replays the graph, updating C in place */
+    int reserved[2];   /* must be zero                                        */
 } dbcsr_opts;
 
 /* Statistics of the last dbcsr_multiply on the calling thread. */
@@ -160,6 +172,11 @@ DBCSR_API int dbcsr_get_index(dbcsr_matrix m, int *blk_row, int *blk_col, int64_
  * memory if out_on_device == 0 and device memory otherwise. */
 DBCSR_API int dbcsr_get_data(dbcsr_matrix m, double *out, int out_on_device);
 
+/* Overwrite all stored values (nelems doubles, storage order) from `data`,
+ * host memory if data_on_device == 0, else device memory. The pattern is
+ * unchanged, so a kept stack plan (dbcsr_opts.reuse_plan) stays valid. */
+DBCSR_API int dbcsr_set_data(dbcsr_matrix m, const double *data, int data_on_device);
+
 /* Device pointer of the stored values (valid until the next call that changes
  * the matrix) -- for callers that keep data resident on the GPU. */
 DBCSR_API int dbcsr_data_ptr(dbcsr_matrix m, double **dev_ptr);
@@ -187,6 +204,12 @@ DBCSR_API int dbcsr_multiply(char transa, char transb, double alpha, dbcsr_matri
 
 /* Statistics of the last dbcsr_multiply of this thread. */
 DBCSR_API int dbcsr_get_stats(dbcsr_stats *out);
+
+/* Per-shape choice of the FP64 stack kernel (the paper's LIBCUSMM is
+ * auto-tuned per (m, n, k); Sec. II). count entries: C blocks of size
+ * m[q] x n[q] (1..128) use variant[q] (0..3, see dbcsr_opts.kernel).
+ * Replaces the previous table; count = 0 clears it. Host arrays. */
+DBCSR_API int dbcsr_set_tuning(const int *m, const int *n, const int *variant, int count);
 
 /* The stack list of Sec. II (Traversal + Generation), as the GPU builds it
  * for op(A) * op(B): one entry per block product, 7 int32 each:

@@ -178,8 +178,38 @@ int setup_sizes(dbcsr_matrix_s* m, int nbr, int nbc, const int* rs, const int* c
     return DBCSR_OK;
 }
 
+// A kept stack plan: the product list of one multiply and a CUDA graph of its
+// FP64 product kernel, replayed in place on the C it produced while the
+// operands' patterns (uid + version) and the scalars are unchanged.
+struct ReusePlan {
+    uint64_t a_uid = 0, a_ver = 0, b_uid = 0, b_ver = 0, c_ver = 0;
+    bool ta = false, tb = false, use_old = false;
+    double alpha = 0.0, beta = 0.0;
+    int64_t nC = 0, nprod = 0;
+    int64_t* c_pstart = nullptr;
+    int2* prod = nullptr;
+    int* c_ident = nullptr;          // identity map: block b of C is its own old block
+    unsigned long long* counter = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    ~ReusePlan() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        dfree(c_pstart, (size_t)nC + 1);
+        dfree(prod, (size_t)(nprod ? nprod : 1));
+        dfree(c_ident, (size_t)(nC ? nC : 1));
+        dfree(counter, 1);
+    }
+};
+
+void free_plan(dbcsr_matrix_s* m) {
+    delete static_cast<ReusePlan*>(m->plan);
+    m->plan = nullptr;
+}
+
 void destroy(dbcsr_matrix_s* m) {
     if (!m) return;
+    free_plan(m);
     free_index(m);
     dfree(m->d_rs, (size_t)m->nbr + 1);
     dfree(m->d_cs, (size_t)m->nbc + 1);
@@ -380,6 +410,15 @@ int dbcsr_get_data(dbcsr_matrix m, double* out, int out_on_device) {
     return DBCSR_OK;
 }
 
+int dbcsr_set_data(dbcsr_matrix m, const double* data, int data_on_device) {
+    if (!m || (!data && m->nelems)) return fail(DBCSR_ERR_ARG, "set_data: NULL argument");
+    if (m->nelems == 0) return DBCSR_OK;
+    DB_CUDA(cudaMemcpyAsync(m->d_data, data, sizeof(double) * m->nelems,
+                            data_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, g_ctx.stream));
+    DB_TRY(sync_stream());
+    return DBCSR_OK;
+}
+
 int dbcsr_data_ptr(dbcsr_matrix m, double** p) {
     if (!m || !p) return fail(DBCSR_ERR_ARG, "data_ptr: NULL argument");
     *p = m->d_data;
@@ -402,6 +441,11 @@ int dbcsr_get_block(dbcsr_matrix m, int row, int col, double* out, int* found) {
     DB_TRY(sync_stream());
     *found = 1;
     return DBCSR_OK;
+}
+
+int dbcsr_set_tuning(const int* m, const int* n, const int* variant, int count) {
+    if (count < 0 || (count > 0 && (!m || !n || !variant))) return fail(DBCSR_ERR_ARG, "set_tuning: bad arguments");
+    return smm_set_table(m, n, variant, count);
 }
 
 int dbcsr_get_stats(dbcsr_stats* out) {
@@ -509,8 +553,38 @@ double useful_flops_host(bool ta, bool tb, dbcsr_matrix_s* A, dbcsr_matrix_s* B,
     return f;
 }
 
+__global__ void k_iota_i32(int64_t n, int* __restrict__ out) {
+    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b < n) out[b] = (int)b;
+}
+
+bool plan_matches(const ReusePlan* rp, bool ta, bool tb, double alpha, double beta, dbcsr_matrix_s* A,
+                  dbcsr_matrix_s* B, dbcsr_matrix_s* C) {
+    return rp && rp->exec && rp->a_uid == A->uid && rp->a_ver == A->version && rp->b_uid == B->uid &&
+           rp->b_ver == B->version && rp->c_ver == C->version && rp->ta == ta && rp->tb == tb &&
+           rp->alpha == alpha && rp->beta == beta && rp->use_old == (beta != 0.0);
+}
+
 int multiply_stacks(bool ta, bool tb, double alpha, dbcsr_matrix_s* A, dbcsr_matrix_s* B, double beta,
                     dbcsr_matrix_s* C, const dbcsr_opts& o) {
+    const bool reuse = o.reuse_plan != 0 && o.precision == DBCSR_PREC_FP64;
+    if (reuse && plan_matches(static_cast<ReusePlan*>(C->plan), ta, tb, alpha, beta, A, B, C)) {
+        // same patterns into the C this plan produced: replay the product kernel in place
+        ReusePlan* rp = static_cast<ReusePlan*>(C->plan);
+        mark(0);
+        mark(1);
+        timer_kernel_begin();
+        DB_CUDA(cudaGraphLaunch(rp->exec, g_ctx.stream));
+        count_launch();
+        timer_kernel_end();
+        mark(2);
+        mark(3);
+        g_stats.main_flops = g_stats.useful_flops;
+        g_stats.main_bytes = 8.0 * ((double)A->nelems + (double)B->nelems + (double)C->nelems *
+                                                                              (rp->use_old ? 2.0 : 1.0));
+        g_stats.c_blocks = C->nblks;
+        return DBCSR_OK;
+    }
     if (ta) DB_TRY(build_transpose_index(A));
     if (tb) DB_TRY(build_transpose_index(B));
     OpView va = make_view(A, ta), vb = make_view(B, tb);
@@ -544,7 +618,9 @@ int multiply_stacks(bool ta, bool tb, double alpha, dbcsr_matrix_s* A, dbcsr_mat
     int rc;
     mark(1);
     if (o.precision == DBCSR_PREC_FP64) {
-        rc = smm_fp64_generic(g, C->max_rs * C->max_cs);
+        timer_kernel_begin();
+        rc = smm_fp64_dispatch(g, C->max_rs * C->max_cs, o.kernel);
+        timer_kernel_end();
         g_stats.main_flops = g_stats.useful_flops;
     } else {
         rc = smm_emulated(g, A, ta, B, tb, C, o, nullptr);
@@ -572,8 +648,64 @@ int multiply_stacks(bool ta, bool tb, double alpha, dbcsr_matrix_s* A, dbcsr_mat
     const int64_t nC = P.nC, ne = P.nelem;
     P.nC = 0;   // arrays above no longer belong to P
     dfree(P.c_old, (size_t)(nC ? nC : 1));
-    dfree(P.c_pstart, (size_t)nC + 1);
+    int64_t* pstart = P.c_pstart;
+    P.c_pstart = nullptr;
+    free_plan(C);
     install(C, nC, ne, rowptr, col, row_of, off, data);
+    if (!reuse) {
+        dfree(pstart, (size_t)nC + 1);
+        mark(3);
+        return DBCSR_OK;
+    }
+    // keep the product list with C and capture the in-place product kernel
+    auto* rp = new ReusePlan();
+    rp->a_uid = A->uid; rp->a_ver = A->version; rp->b_uid = B->uid; rp->b_ver = B->version;
+    rp->c_ver = C->version; rp->ta = ta; rp->tb = tb; rp->alpha = alpha; rp->beta = beta;
+    rp->use_old = beta != 0.0;
+    rp->nC = nC;
+    rp->nprod = P.nprod;
+    rp->c_pstart = pstart;
+    rp->prod = P.prod;
+    P.prod = nullptr;
+    P.nprod = 0;
+    C->plan = rp;
+    DB_TRY(dalloc(&rp->c_ident, (size_t)(nC ? nC : 1)));
+    DB_TRY(dalloc(&rp->counter, 1));
+    if (nC > 0) {
+        k_iota_i32<<<(unsigned)cdiv(nC, 256), 256, 0, g_ctx.stream>>>(nC, rp->c_ident);
+        DB_KCHECK();
+    }
+    SmmArgs r = g;
+    r.c_row = C->d_row_of;
+    r.c_col = C->d_col;
+    r.c_off = C->d_off;
+    r.c_pstart = rp->c_pstart;
+    r.prod = rp->prod;
+    r.Cd = C->d_data;
+    r.c_old = rp->use_old ? rp->c_ident : nullptr;
+    r.Cold = rp->use_old ? C->d_data : nullptr;      // in place: each owner reads then writes its block
+    r.Cold_off = rp->use_old ? C->d_off : nullptr;
+    r.counter = rp->counter;
+    DB_CUDA(cudaStreamSynchronize(g_ctx.stream));
+    cudaStream_t cap;
+    DB_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaStream_t saved = g_ctx.stream;
+    g_ctx.stream = cap;
+    int rc2 = DBCSR_OK;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaMemsetAsync(rp->counter, 0, sizeof(unsigned long long), cap);
+        rc2 = smm_fp64_generic(r, C->max_rs * C->max_cs);
+        e = cudaStreamEndCapture(cap, &rp->graph);
+        if (e == cudaSuccess && rc2 == DBCSR_OK) e = cudaGraphInstantiate(&rp->exec, rp->graph, 0);
+    }
+    g_ctx.stream = saved;
+    cudaStreamDestroy(cap);
+    if (e != cudaSuccess || rc2 != DBCSR_OK) {
+        cudaGetLastError();
+        free_plan(C);
+        return rc2 != DBCSR_OK ? rc2 : fail(DBCSR_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+    }
     mark(3);
     return DBCSR_OK;
 }

@@ -233,9 +233,10 @@ int dgemm_ozaki(int64_t M, int64_t N, int64_t K, double alpha, const double* A, 
         DB_KCHECK();
     }
     const int tn = 128;
+    const int cm = tc_cluster_m(M);
     CUtensorMap tmA, tmB;
     DB_TRY(make_slice_tmap(&tmA, SA.p, ldk, M, s, 128, 2));
-    DB_TRY(make_slice_tmap(&tmB, SB.p, ldk, N, s, tn, 2));
+    DB_TRY(make_slice_tmap(&tmB, SB.p, ldk, N, s, tn / cm, 2));
     OzParams p{};
     p.chunk_blocks = OZ_CHUNK_BLOCKS;
     p.elem_bytes = 2;
@@ -255,7 +256,7 @@ int dgemm_ozaki(int64_t M, int64_t N, int64_t K, double alpha, const double* A, 
     p.err = ctx().d_flags;
     DB_CUDA(cudaMemsetAsync(p.err, 0, sizeof(int), st));
     timer_kernel_begin();
-    DB_TRY(oz_gemm_launch(tmA, tmB, p, tn));
+    DB_TRY(oz_gemm_launch(tmA, tmB, p, cm));
     timer_kernel_end();
     int h_err = 0;
     DB_CUDA(cudaMemcpyAsync(&h_err, p.err, sizeof(int), cudaMemcpyDeviceToHost, st));

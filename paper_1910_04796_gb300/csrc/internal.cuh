@@ -135,6 +135,7 @@ struct dbcsr_matrix_s {
     std::vector<int64_t> h_off;
     uint64_t version = 0;    // bumped whenever the pattern changes
     uint64_t uid = 0;
+    void* plan = nullptr;    // reusable stack plan + CUDA graph (api.cu)
 };
 
 namespace dbcsr {

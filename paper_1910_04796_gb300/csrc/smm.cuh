@@ -24,6 +24,14 @@ struct SmmArgs {
     unsigned long long* counter;  // zeroed work counter
 };
 
+// FP64 stack-kernel variants (the autotuner's search space), see smm_fp64.cu
+constexpr int SMM_NUM_VARIANTS = 4;
+
+// variant 0 over every C block
 int smm_fp64_generic(const SmmArgs& g, int max_mn);
+// kernel = 0: per-(m,n) table (variant 0 where untuned); kernel = v >= 1: variant v-1
+int smm_fp64_dispatch(const SmmArgs& g, int max_mn, int kernel);
+// (m, n) -> variant entries of the tuning table (replaces the table)
+int smm_set_table(const int* m, const int* n, const int* variant, int count);
 
 }  // namespace dbcsr

@@ -73,8 +73,15 @@ struct ModeTraits<MODE_TF32> {
     }
 };
 
-__device__ __forceinline__ void unit_coords(int64_t u, const OzParams& p, int& tm, int& tn, int& kseg, int& li) {
-    const int64_t tiles = (int64_t)p.tiles_m * p.tiles_n;
+// Work unit u -> (tile row, tile column, K segment, level). With clusters of CM
+// CTAs along M, a unit covers CM vertically adjacent tiles: CTA `rank` of the
+// cluster takes tile row tm * CM + rank, and all CTAs of a cluster walk the
+// same unit sequence (same tile column, level and K range, hence the same
+// B tile, which they share through multicast).
+__device__ __forceinline__ void unit_coords(int64_t u, const OzParams& p, int cm, int rank, int& tm, int& tn,
+                                            int& kseg, int& li) {
+    const int tiles_mc = (p.tiles_m + cm - 1) / cm;
+    const int64_t tiles = (int64_t)tiles_mc * p.tiles_n;
     int64_t x = u % tiles;
     int64_t r = u / tiles;
     kseg = (int)(r % p.ksegs);
@@ -83,17 +90,20 @@ __device__ __forceinline__ void unit_coords(int64_t u, const OzParams& p, int& t
     const int64_t per_group = (int64_t)TC_GROUP_M * p.tiles_n;
     const int64_t g = x / per_group;
     const int first_m = (int)(g * TC_GROUP_M);
-    const int gm = min(TC_GROUP_M, p.tiles_m - first_m);
+    const int gm = min(TC_GROUP_M, tiles_mc - first_m);
     const int64_t xi = x - g * per_group;
-    tm = first_m + (int)(xi % gm);
+    tm = (first_m + (int)(xi % gm)) * cm + rank;
     tn = (int)(xi / gm);
 }
 
-template <int MODE>
+template <int MODE, int CM>
 __global__ void __launch_bounds__(TcCfg::THREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, OzParams p) {
     using Cfg = TcCfg;
     using Tr = ModeTraits<MODE>;
+    const int rank = (CM > 1) ? (int)ptx::cluster_ctarank() : 0;
+    const int64_t cl_id = blockIdx.x / CM, n_cl = gridDim.x / CM;
+    const uint16_t cl_mask = (uint16_t)((1u << CM) - 1u);
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* sA = smem;
@@ -110,7 +120,7 @@ __global__ void __launch_bounds__(TcCfg::THREADS, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < Cfg::STAGES; s++) {
             ptx::mbar_init(&full[s], 1);
-            ptx::mbar_init(&empty[s], 1);
+            ptx::mbar_init(&empty[s], CM);   // released by the MMA of every CTA sharing the stage
         }
         for (int b = 0; b < 2; b++) {
             ptx::mbar_init(&tfull[b], 1);
@@ -130,6 +140,7 @@ __global__ void __launch_bounds__(TcCfg::THREADS, 1)
     }
     ptx::tc_fence_before();
     __syncthreads();
+    if (CM > 1) ptx::cluster_sync();   // peers' barriers initialised before any multicast
     ptx::tc_fence_after();
     const uint32_t tmem = *tmem_holder;
     const int kelems = TC_ROW_BYTES / p.elem_bytes;   // K elements per k-block
@@ -144,9 +155,9 @@ __global__ void __launch_bounds__(TcCfg::THREADS, 1)
         if (lane == 0) {
             int64_t it = 0;
             bool ok = true;
-            for (int64_t u = blockIdx.x; u < p.units && ok; u += gridDim.x) {
+            for (int64_t u = cl_id; u < p.units && ok; u += n_cl) {
                 int tm, tn, kseg, li;
-                unit_coords(u, p, tm, tn, kseg, li);
+                unit_coords(u, p, CM, rank, tm, tn, kseg, li);
                 const int d = li + 2;
                 const int kb0 = kseg * p.kseg_blocks;
                 const int kb1 = min(kb0 + p.kseg_blocks, p.kblocks);
@@ -161,7 +172,16 @@ __global__ void __launch_bounds__(TcCfg::THREADS, 1)
                         }
                         ptx::mbar_arrive_expect_tx(&full[st], Cfg::STAGE_A + Cfg::STAGE_B);
                         ptx::tma_load_3d(sA + st * Cfg::STAGE_A, &tmA, &full[st], kb * kelems, tm * TC_TM, t - 1);
-                        ptx::tma_load_3d(sB + st * Cfg::STAGE_B, &tmB, &full[st], kb * kelems, tn * TC_TN, d - t - 1);
+                        if (CM == 1) {
+                            ptx::tma_load_3d(sB + st * Cfg::STAGE_B, &tmB, &full[st], kb * kelems, tn * TC_TN,
+                                             d - t - 1);
+                        } else {
+                            // this CTA's share of the common B tile, written into every CTA of the cluster
+                            const int rows = TC_TN / CM;
+                            ptx::tma_load_3d_multicast(sB + st * Cfg::STAGE_B + rank * rows * TC_ROW_BYTES, &tmB,
+                                                       &full[st], kb * kelems, tn * TC_TN + rank * rows, d - t - 1,
+                                                       cl_mask);
+                        }
                     }
                 }
             }
@@ -180,9 +200,9 @@ __global__ void __launch_bounds__(TcCfg::THREADS, 1)
         if (lane == 0) {
             int64_t it = 0, ci = 0;
             bool ok = true;
-            for (int64_t u = blockIdx.x; u < p.units && ok; u += gridDim.x) {
+            for (int64_t u = cl_id; u < p.units && ok; u += n_cl) {
                 int tm, tn, kseg, li;
-                unit_coords(u, p, tm, tn, kseg, li);
+                unit_coords(u, p, CM, rank, tm, tn, kseg, li);
                 const int d = li + 2;
                 const int kb0 = kseg * p.kseg_blocks;
                 const int kb1 = min(kb0 + p.kseg_blocks, p.kblocks);
@@ -215,7 +235,9 @@ __global__ void __launch_bounds__(TcCfg::THREADS, 1)
                                 Tr::mma(dt, ad + (uint64_t)((kk * 32) >> 4), bd + (uint64_t)((kk * 32) >> 4),
                                         (kb > c || kk > 0) ? 1u : 0u);
                             }
-                            ptx::mma_commit(&empty[st]);
+                            // the stage is free once every CTA that shares it has consumed it
+                            if (CM == 1) ptx::mma_commit(&empty[st]);
+                            else ptx::mma_commit_multicast(&empty[st], cl_mask);
                         }
                         if (ok) ptx::mma_commit(&tfull[buf]);
                     }
@@ -232,9 +254,9 @@ __global__ void __launch_bounds__(TcCfg::THREADS, 1)
         const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
         int64_t ci = 0;
         bool ok = true;
-        for (int64_t u = blockIdx.x; u < p.units && ok; u += gridDim.x) {
+        for (int64_t u = cl_id; u < p.units && ok; u += n_cl) {
             int tm, tn, kseg, li;
-            unit_coords(u, p, tm, tn, kseg, li);
+            unit_coords(u, p, CM, rank, tm, tn, kseg, li);
             const int d = li + 2;
             const int kb0 = kseg * p.kseg_blocks;
             const int kb1 = min(kb0 + p.kseg_blocks, p.kblocks);
@@ -311,6 +333,8 @@ __global__ void __launch_bounds__(TcCfg::THREADS, 1)
     }
     ptx::tc_fence_before();
     __syncthreads();
+    // no CTA leaves while a peer may still write into its shared memory or barriers
+    if (CM > 1) ptx::cluster_sync();
     ptx::tc_fence_after();
     if (warp == 1) ptx::tmem_dealloc(tmem, Cfg::TMEM_COLS);
 }
@@ -335,12 +359,38 @@ int get_encoder(EncodeTiledFn* fn) {
     return DBCSR_OK;
 }
 
-template <int MODE>
+// CM = CTAs per cluster along M (1, or 2 with the B tile multicast); tmB's
+// box must then hold TC_TN / CM rows.
+template <int MODE, int CM>
 int launch_mode(const CUtensorMap& tmA, const CUtensorMap& tmB, const OzParams& p, cudaStream_t st, int num_sms) {
-    if (p.units <= 0) return DBCSR_OK;
-    const int grid = (int)std::min<int64_t>(p.units, num_sms);
-    DB_CUDA(cudaFuncSetAttribute(k_tc_gemm<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg::SMEM));
-    k_tc_gemm<MODE><<<grid, TcCfg::THREADS, TcCfg::SMEM, st>>>(tmA, tmB, p);
+    OzParams q = p;
+    q.units = cdiv(p.tiles_m, CM) * p.tiles_n * p.ksegs * p.s;
+    if (q.units <= 0) return DBCSR_OK;
+    const int clusters = (int)std::min<int64_t>(q.units, num_sms / CM);
+    auto kern = k_tc_gemm<MODE, CM>;
+    DB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg::SMEM));
+    if (CM == 1) {
+        kern<<<clusters, TcCfg::THREADS, TcCfg::SMEM, st>>>(tmA, tmB, q);
+    } else {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(clusters * CM));
+        cfg.blockDim = dim3(TcCfg::THREADS);
+        cfg.dynamicSmemBytes = TcCfg::SMEM;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = CM;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        // persistent clusters: no more than can be resident at once
+        int active = 0;
+        DB_CUDA(cudaOccupancyMaxActiveClusters(&active, kern, &cfg));
+        if (active < 1) return fail(DBCSR_ERR_CUDA, "tensor-core GEMM: no cluster of 2 CTAs fits on this GPU");
+        if (active < clusters) cfg.gridDim = dim3((unsigned)(active * CM));
+        DB_CUDA(cudaLaunchKernelEx(&cfg, kern, tmA, tmB, q));
+    }
     DB_KCHECK();
     return DBCSR_OK;
 }
@@ -366,18 +416,21 @@ int make_slice_tmap(CUtensorMap* map, const void* base, int64_t ldk, int64_t row
     return DBCSR_OK;
 }
 
-int oz_gemm_launch(const CUtensorMap& tmA, const CUtensorMap& tmB, const OzParams& p, int tn) {
-    if (tn != TC_TN) return fail(DBCSR_ERR_ARG, "slice gemm: unsupported tile width");
-    return launch_mode<MODE_SLICES>(tmA, tmB, p, ctx().stream, ctx().num_sms);
+int oz_gemm_launch(const CUtensorMap& tmA, const CUtensorMap& tmB, const OzParams& p, int cluster_m) {
+    if (cluster_m == 2) return launch_mode<MODE_SLICES, 2>(tmA, tmB, p, ctx().stream, ctx().num_sms);
+    return launch_mode<MODE_SLICES, 1>(tmA, tmB, p, ctx().stream, ctx().num_sms);
 }
 
 int oz_gemm_launch_on(const CUtensorMap& tmA, const CUtensorMap& tmB, const OzParams& p, cudaStream_t st,
                       int num_sms) {
-    return launch_mode<MODE_SLICES>(tmA, tmB, p, st, num_sms);
+    return launch_mode<MODE_SLICES, 1>(tmA, tmB, p, st, num_sms);
 }
 
-int tf32_gemm_launch(const CUtensorMap& tmA, const CUtensorMap& tmB, const OzParams& p) {
-    return launch_mode<MODE_TF32>(tmA, tmB, p, ctx().stream, ctx().num_sms);
+int tf32_gemm_launch(const CUtensorMap& tmA, const CUtensorMap& tmB, const OzParams& p, int cluster_m) {
+    if (cluster_m == 2) return launch_mode<MODE_TF32, 2>(tmA, tmB, p, ctx().stream, ctx().num_sms);
+    return launch_mode<MODE_TF32, 1>(tmA, tmB, p, ctx().stream, ctx().num_sms);
 }
+
+int tc_cluster_m(int64_t M) { return cdiv(M, TC_TM) >= 2 ? 2 : 1; }
 
 }  // namespace dbcsr

@@ -64,7 +64,8 @@ int dgemm_tf32(int64_t M, int64_t N, int64_t K, double alpha, const double* A, i
     DB_KCHECK();
     CUtensorMap tmA, tmB;
     DB_TRY(make_slice_tmap(&tmA, AT.p, ldk, M, 1, 128, 4));
-    DB_TRY(make_slice_tmap(&tmB, BT.p, ldk, N, 1, 128, 4));
+    const int cm = tc_cluster_m(M);
+    DB_TRY(make_slice_tmap(&tmB, BT.p, ldk, N, 1, 128 / cm, 4));
     OzParams p{};
     p.M = (int)M;
     p.N = (int)N;
@@ -84,7 +85,7 @@ int dgemm_tf32(int64_t M, int64_t N, int64_t K, double alpha, const double* A, i
     p.err = ctx().d_flags;
     DB_CUDA(cudaMemsetAsync(p.err, 0, sizeof(int), st));
     timer_kernel_begin();
-    DB_TRY(tf32_gemm_launch(tmA, tmB, p));
+    DB_TRY(tf32_gemm_launch(tmA, tmB, p, cm));
     timer_kernel_end();
     int h_err = 0;
     DB_CUDA(cudaMemcpyAsync(&h_err, p.err, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -30,7 +30,7 @@ class DbcsrError(RuntimeError):
 
 class Opts(C.Structure):
     _fields_ = [("path", C.c_int), ("precision", C.c_int), ("ozaki_slices", C.c_int),
-                ("kernel", C.c_int), ("timing", C.c_int), ("reserved", C.c_int * 3)]
+                ("kernel", C.c_int), ("timing", C.c_int), ("reuse_plan", C.c_int), ("reserved", C.c_int * 2)]
 
 
 class Stats(C.Structure):
@@ -61,10 +61,12 @@ SIGNATURES = [
     ("dbcsr_get_info", C.c_int, [_P, _IP, _IP, _LP, _LP]),
     ("dbcsr_get_index", C.c_int, [_P, _IP, _IP, _LP]),
     ("dbcsr_get_data", C.c_int, [_P, _P, C.c_int]),
+    ("dbcsr_set_data", C.c_int, [_P, _P, C.c_int]),
     ("dbcsr_data_ptr", C.c_int, [_P, C.POINTER(_P)]),
     ("dbcsr_get_block", C.c_int, [_P, C.c_int, C.c_int, _DP, _IP]),
     ("dbcsr_multiply", C.c_int, [C.c_char, C.c_char, C.c_double, _P, _P, C.c_double, _P, C.POINTER(Opts)]),
     ("dbcsr_get_stats", C.c_int, [C.POINTER(Stats)]),
+    ("dbcsr_set_tuning", C.c_int, [_IP, _IP, _IP, C.c_int]),
     ("dbcsr_get_stacks", C.c_int, [C.c_char, C.c_char, _P, _P, C.c_int, _IP, C.c_int64, _LP]),
     ("dbcsr_dgemm_emulated_noalloc", C.c_int, [C.c_int64, C.c_int64, C.c_int64, C.c_double, _P, C.c_int64, _P,
                                                C.c_int64, C.c_double, _P, C.c_int64, C.c_int, _P]),
@@ -219,6 +221,14 @@ class Matrix:
         _check(load().dbcsr_get_data(self._h, C.c_void_p(out.data_ptr()), 1))
         return out[:e]
 
+    def set_data(self, data):
+        """Overwrite the stored values (numpy host array or CUDA float64 tensor, storage order)."""
+        if hasattr(data, "is_cuda") and data.is_cuda:
+            _check(load().dbcsr_set_data(self._h, C.c_void_p(data.data_ptr()), 1))
+        else:
+            d = np.ascontiguousarray(data, np.float64)
+            _check(load().dbcsr_set_data(self._h, d.ctypes.data_as(C.c_void_p), 0))
+
     def data_ptr(self) -> int:
         p = C.c_void_p()
         _check(load().dbcsr_data_ptr(self._h, C.byref(p)))
@@ -231,9 +241,10 @@ class Matrix:
         return out.reshape((m, n), order="F") if found.value else None
 
 
-def opts(path="auto", precision="fp64", ozaki_slices=0, kernel=0, timing=False) -> Opts:
+def opts(path="auto", precision="fp64", ozaki_slices=0, kernel=0, timing=False, reuse_plan=False) -> Opts:
     o = Opts()
     o.timing = 1 if timing else 0
+    o.reuse_plan = 1 if reuse_plan else 0
     o.path = _PATH[path] if isinstance(path, str) else int(path)
     o.precision = _PREC[precision] if isinstance(precision, str) else int(precision)
     o.ozaki_slices = ozaki_slices
@@ -242,11 +253,18 @@ def opts(path="auto", precision="fp64", ozaki_slices=0, kernel=0, timing=False) 
 
 
 def multiply(transa, transb, alpha, A: Matrix, B: Matrix, beta, Cm: Matrix, path="auto", precision="fp64",
-             ozaki_slices=0, kernel=0, timing=False):
+             ozaki_slices=0, kernel=0, timing=False, reuse_plan=False):
     """C = alpha*op(A)*op(B) + beta*C on the GPU (see dbcsr_multiply)."""
-    o = opts(path, precision, ozaki_slices, kernel, timing)
+    o = opts(path, precision, ozaki_slices, kernel, timing, reuse_plan)
     _check(load().dbcsr_multiply(transa.encode(), transb.encode(), float(alpha), A.handle, B.handle,
                                  float(beta), Cm.handle, C.byref(o)))
+
+
+def set_tuning(entries):
+    """FP64 stack-kernel variant per C-block shape: iterable of (m, n, variant)."""
+    e = np.asarray(list(entries), np.int32).reshape(-1, 3)
+    m, n, v = (np.ascontiguousarray(e[:, q]) for q in range(3))
+    _check(load().dbcsr_set_tuning(_ip(m), _ip(n), _ip(v), len(e)))
 
 
 def stats() -> dict:
