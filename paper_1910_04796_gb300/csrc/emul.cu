@@ -165,6 +165,51 @@ __global__ void k_recombine(int64_t M, int64_t N, int s, int ksegs, const double
     C[i + j * ldc] = v;
 }
 
+// 2^k as a double for -1022 <= k <= 1023 (exact bit pattern)
+__device__ __forceinline__ double pow2(int k) { return __longlong_as_double((long long)(1023 + k) << 52); }
+
+// acc * 2^k rounded once, like ldexp(acc, k): a product by an exact normal
+// power of two is correctly rounded; outside that range ldexp itself is used
+__device__ __forceinline__ double scale2(double acc, int k) {
+    return (k >= -1022 && k <= 1023) ? acc * pow2(k) : ldexp(acc, k);
+}
+
+// Recombination from int32 row-major level sums ws[d-2][kseg][i][j] (row
+// stride ldws) into column-major C, through a 32 x 32 shared-memory tile so
+// that both the reads and the writes are coalesced. Same arithmetic and order
+// as k_recombine.
+__global__ void __launch_bounds__(256) k_recombine_rm(int64_t M, int64_t N, int s, int ksegs, const int* __restrict__ ws,
+                                                      int64_t ldws, const int* __restrict__ e,
+                                                      const int* __restrict__ f, double alpha, double beta,
+                                                      double* __restrict__ C, int64_t ldc) {
+    __shared__ double tile[32][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+    const int64_t i0 = (int64_t)blockIdx.y * 32, j0 = (int64_t)blockIdx.x * 32;
+    const int64_t lstride = M * ldws;
+    for (int r = ty; r < 32; r += 8) {
+        const int64_t i = i0 + r, j = j0 + tx;
+        double acc = 0.0;
+        if (i < M && j < N) {
+            for (int d = s + 1; d >= 2; d--) {
+                int64_t g = 0;   // exact: sum over K segments of int32 partial sums
+                for (int k = 0; k < ksegs; k++) g += ws[((int64_t)(d - 2) * ksegs + k) * lstride + i * ldws + j];
+                acc = fma((double)g, pow2(-7 * d), acc);
+            }
+            acc = scale2(acc, e[i] + f[j]);
+        }
+        tile[r][tx] = acc;
+    }
+    __syncthreads();
+    for (int cc = ty; cc < 32; cc += 8) {
+        const int64_t i = i0 + tx, j = j0 + cc;
+        if (i < M && j < N) {
+            double v = __dmul_rn(alpha, tile[tx][cc]);
+            if (beta != 0.0) v = __dadd_rn(v, __dmul_rn(beta, C[i + j * ldc]));
+            C[i + j * ldc] = v;
+        }
+    }
+}
+
 __global__ void k_scale_c(int64_t M, int64_t N, double beta, double* __restrict__ C, int64_t ldc) {
     const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (idx >= M * N) return;
@@ -232,8 +277,11 @@ int dgemm_ozaki(int64_t M, int64_t N, int64_t K, double alpha, const double* A, 
         k_slice_cols<<<g2, 256, 0, st>>>(N, K, ldk, B, ldb, f.p, s, SB.p);
         DB_KCHECK();
     }
-    const int tn = 128;
-    const int cm = tc_cluster_m(M);
+    // 128 x 256 tiles when the output is wide enough (fewer bytes moved per
+    // flop), else 128 x 128 tiles in clusters of two sharing the B tile
+    const bool wide = N >= 256 && tc256_usable();
+    const int tn = wide ? 256 : 128;
+    const int cm = wide ? 1 : tc_cluster_m(M);
     CUtensorMap tmA, tmB;
     DB_TRY(make_slice_tmap(&tmA, SA.p, ldk, M, s, 128, 2));
     DB_TRY(make_slice_tmap(&tmB, SB.p, ldk, N, s, tn / cm, 2));
@@ -249,24 +297,40 @@ int dgemm_ozaki(int64_t M, int64_t N, int64_t K, double alpha, const double* A, 
     p.tiles_m = (int)cdiv(M, 128);
     p.tiles_n = (int)cdiv(N, tn);
     p.units = (int64_t)p.tiles_m * p.tiles_n * p.ksegs * s;
+    if (p.units >= INT32_MAX) return fail(DBCSR_ERR_OVERFLOW, "emulated gemm: too many work units");
     p.ws_stride = M * N;
-    DBuf<double> ws;
-    DB_TRY(ws.alloc((size_t)s * p.ksegs * M * N));
-    p.ws = ws.p;
     p.err = ctx().d_flags;
     DB_CUDA(cudaMemsetAsync(p.err, 0, sizeof(int), st));
-    timer_kernel_begin();
-    DB_TRY(oz_gemm_launch(tmA, tmB, p, cm));
-    timer_kernel_end();
     int h_err = 0;
-    DB_CUDA(cudaMemcpyAsync(&h_err, p.err, sizeof(int), cudaMemcpyDeviceToHost, st));
-    k_recombine<<<(unsigned)cdiv(M * N, 256), 256, 0, st>>>(M, N, s, p.ksegs, ws.p, p.ws_stride, e.p, f.p, alpha,
-                                                           beta, C, ldc);
-    DB_KCHECK();
+    if (wide) {
+        p.ldws = cdiv(N, 256) * 256;
+        DBuf<int> wsi;
+        DB_TRY(wsi.alloc((size_t)s * p.ksegs * M * p.ldws));
+        p.ws_i32 = wsi.p;
+        timer_kernel_begin();
+        DB_TRY(oz_gemm256_launch(tmA, tmB, p));
+        timer_kernel_end();
+        DB_CUDA(cudaMemcpyAsync(&h_err, p.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        dim3 g((unsigned)cdiv(N, 32), (unsigned)cdiv(M, 32));
+        if (g.y > 65535) return fail(DBCSR_ERR_OVERFLOW, "emulated gemm: M too large for the recombination grid");
+        k_recombine_rm<<<g, 256, 0, st>>>(M, N, s, p.ksegs, wsi.p, p.ldws, e.p, f.p, alpha, beta, C, ldc);
+        DB_KCHECK();
+    } else {
+        DBuf<double> ws;
+        DB_TRY(ws.alloc((size_t)s * p.ksegs * M * N));
+        p.ws = ws.p;
+        timer_kernel_begin();
+        DB_TRY(oz_gemm_launch(tmA, tmB, p, cm));
+        timer_kernel_end();
+        DB_CUDA(cudaMemcpyAsync(&h_err, p.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        k_recombine<<<(unsigned)cdiv(M * N, 256), 256, 0, st>>>(M, N, s, p.ksegs, ws.p, p.ws_stride, e.p, f.p,
+                                                               alpha, beta, C, ldc);
+        DB_KCHECK();
+    }
     DB_CUDA(cudaStreamSynchronize(st));
     if (h_err) return fail(DBCSR_ERR_TIMEOUT, "emulated gemm: a tensor-core pipeline wait timed out");
-    if (main_flops) *main_flops = 2.0 * (double)(p.tiles_m * 128) * (double)(p.tiles_n * tn) * (double)ldk *
-                                  (double)(s * (s + 1) / 2);
+    // algorithmic slice-GEMM flops: one M x N x K product per slice pair (unpadded)
+    if (main_flops) *main_flops = 2.0 * (double)M * (double)N * (double)K * (double)(s * (s + 1) / 2);
     return DBCSR_OK;
 }
 

@@ -170,11 +170,42 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Stage the s slices of product p's A and B blocks into one shared-memory
+// buffer (16-byte cp.async chunks, rows padded to SE_RS).
+template <int S>
+__device__ __forceinline__ void stage_product(const SeArgs& a, int64_t p, int m, int n, __nv_bfloat16* sA,
+                                              __nv_bfloat16* sB, int tid) {
+    const int2 pr = a.prod[p];
+    const int kk = (int)((a.a_off[pr.x + 1] - a.a_off[pr.x]) / m);
+    const int kp = ru16(kk), mp = ru16(m), np = ru16(n);
+    const int cpr = kp / 8;   // chunks per row
+    const int na = S * mp * cpr, nb = S * np * cpr;
+    const __nv_bfloat16* ga = a.SA + a.soffA[pr.x];
+    const __nv_bfloat16* gb = a.SB + a.soffB[pr.y];
+    for (int c = tid; c < na + nb; c += SE_THREADS) {
+        if (c < na) {
+            const int t = c / (mp * cpr), rem = c % (mp * cpr), x = rem / cpr, ch = rem % cpr;
+            cp_async16(sA + (t * SE_MAXB + x) * SE_RS + ch * 8, ga + (int64_t)t * a.totA + x * kp + ch * 8);
+        } else {
+            const int c2 = c - na;
+            const int t = c2 / (np * cpr), rem = c2 % (np * cpr), x = rem / cpr, ch = rem % cpr;
+            cp_async16(sB + (t * SE_MAXB + x) * SE_RS + ch * 8, gb + (int64_t)t * a.totB + x * kp + ch * 8);
+        }
+    }
+}
+
 template <int S>
 __global__ void __launch_bounds__(SE_THREADS) k_smm_emul(SeArgs a) {
     extern __shared__ __align__(16) unsigned char se_smem[];
-    __nv_bfloat16* sA = reinterpret_cast<__nv_bfloat16*>(se_smem);          // [S][32][SE_RS]
-    __nv_bfloat16* sB = sA + S * SE_MAXB * SE_RS;                             // [S][32][SE_RS]
+    // two buffers, each [S][32][SE_RS] for A then [S][32][SE_RS] for B
+    __nv_bfloat16* buf0 = reinterpret_cast<__nv_bfloat16*>(se_smem);
+    constexpr int BUF = 2 * S * SE_MAXB * SE_RS;
     __shared__ int s_cb;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int wm = warp & 1, wn = warp >> 1;
@@ -201,29 +232,39 @@ __global__ void __launch_bounds__(SE_THREADS) k_smm_emul(SeArgs a) {
                     gi[d][nt][r] = 0;
                 }
         int since = 0;
+        if (p0 < p1) stage_product<S>(a, p0, m, n, buf0, buf0 + S * SE_MAXB * SE_RS, tid);
+        cp_async_commit();
         for (int64_t p = p0; p < p1; p++) {
-            const int2 pr = a.prod[p];
-            const int kk = (int)((a.a_off[pr.x + 1] - a.a_off[pr.x]) / m);
-            const int kp = ru16(kk), mp = ru16(m), np = ru16(n);
-            // stage the s slices of both blocks (16-byte chunks, padded rows)
-            const int cpr = kp / 8;   // chunks per row
-            const int na = S * mp * cpr, nb = S * np * cpr;
-            const __nv_bfloat16* ga = a.SA + a.soffA[pr.x];
-            const __nv_bfloat16* gb = a.SB + a.soffB[pr.y];
-            for (int c = tid; c < na + nb; c += SE_THREADS) {
-                if (c < na) {
-                    const int t = c / (mp * cpr), rem = c % (mp * cpr), x = rem / cpr, ch = rem % cpr;
-                    cp_async16(sA + (t * SE_MAXB + x) * SE_RS + ch * 8, ga + (int64_t)t * a.totA + x * kp + ch * 8);
-                } else {
-                    const int c2 = c - na;
-                    const int t = c2 / (np * cpr), rem = c2 % (np * cpr), x = rem / cpr, ch = rem % cpr;
-                    cp_async16(sB + (t * SE_MAXB + x) * SE_RS + ch * 8, gb + (int64_t)t * a.totB + x * kp + ch * 8);
-                }
+            const int cur = (int)((p - p0) & 1);
+            __nv_bfloat16* sA = buf0 + cur * BUF;
+            __nv_bfloat16* sB = sA + S * SE_MAXB * SE_RS;
+            // prefetch the next product into the other buffer while this one computes
+            if (p + 1 < p1) {
+                __nv_bfloat16* nA = buf0 + (cur ^ 1) * BUF;
+                stage_product<S>(a, p + 1, m, n, nA, nA + S * SE_MAXB * SE_RS, tid);
             }
-            cp_async_wait_all();
+            cp_async_commit();
+            cp_async_wait_group<1>();
             __syncthreads();
             if (active) {
-                const int nks = kp / 16;
+                const int2 pr = a.prod[p];
+                const int kk = (int)((a.a_off[pr.x + 1] - a.a_off[pr.x]) / m);
+                const int nks = ru16(kk) / 16;
+                // every B-slice fragment of this warp's 16 columns, once per product
+                uint32_t bf[S][2][2][2];
+#pragma unroll
+                for (int u = 0; u < S; u++)
+#pragma unroll
+                    for (int nt = 0; nt < 2; nt++)
+#pragma unroll
+                        for (int ks = 0; ks < 2; ks++) {
+                            if (ks < nks) {
+                                const __nv_bfloat16* bb =
+                                    sB + (u * SE_MAXB + wn * 16 + nt * 8 + g) * SE_RS + ks * 16 + 2 * q;
+                                bf[u][nt][ks][0] = *reinterpret_cast<const uint32_t*>(bb);
+                                bf[u][nt][ks][1] = *reinterpret_cast<const uint32_t*>(bb + 8);
+                            }
+                        }
 #pragma unroll
                 for (int t = 0; t < S; t++) {
                     uint32_t af[2][4];
@@ -238,25 +279,15 @@ __global__ void __launch_bounds__(SE_THREADS) k_smm_emul(SeArgs a) {
                         }
                     }
 #pragma unroll
-                    for (int u = 0; u < S - t; u++) {
+                    for (int u = 0; u < S - t; u++)
 #pragma unroll
-                        for (int nt = 0; nt < 2; nt++) {
+                        for (int nt = 0; nt < 2; nt++)
 #pragma unroll
-                            for (int ks = 0; ks < 2; ks++) {
-                                if (ks < nks) {
-                                    const __nv_bfloat16* bb =
-                                        sB + (u * SE_MAXB + wn * 16 + nt * 8 + g) * SE_RS + ks * 16 + 2 * q;
-                                    uint32_t bf[2];
-                                    bf[0] = *reinterpret_cast<const uint32_t*>(bb);
-                                    bf[1] = *reinterpret_cast<const uint32_t*>(bb + 8);
-                                    mma_bf16_16816(acc[t + u][nt], af[ks], bf);
-                                }
-                            }
-                        }
-                    }
+                            for (int ks = 0; ks < 2; ks++)
+                                if (ks < nks) mma_bf16_16816(acc[t + u][nt], af[ks], bf[u][nt][ks]);
                 }
             }
-            __syncthreads();
+            __syncthreads();   // this buffer is refilled two products later
             if (++since == a.flush_every || p + 1 == p1) {
                 since = 0;
 #pragma unroll
@@ -270,6 +301,7 @@ __global__ void __launch_bounds__(SE_THREADS) k_smm_emul(SeArgs a) {
                         }
             }
         }
+        cp_async_wait_group<0>();
         if (!active) continue;
         // FP64 recombination, then alpha / beta, into the column-major C block
         const int64_t rbase = a.croff[i], cbase = a.ccoff[j];
@@ -303,7 +335,7 @@ __global__ void k_max_span(int64_t nC, const int64_t* __restrict__ pstart, unsig
 
 template <int S>
 int launch_se(const SeArgs& a, int grid) {
-    const int smem = 2 * S * SE_MAXB * SE_RS * (int)sizeof(__nv_bfloat16);
+    const int smem = 4 * S * SE_MAXB * SE_RS * (int)sizeof(__nv_bfloat16);   // two buffers of A + B
     DB_CUDA(cudaFuncSetAttribute(k_smm_emul<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     k_smm_emul<S><<<grid, SE_THREADS, smem, ctx().stream>>>(a);
     DB_KCHECK();

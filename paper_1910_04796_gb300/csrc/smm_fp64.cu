@@ -7,19 +7,23 @@
 // the autotuner's table drives.
 //
 // GB300 facts that shape them: FP64 runs at about 1 TFLOP/s on the whole chip
-// (DFMA and DMMA alike), i.e. under two FP64 FMAs per clock per SM, so a small
-// block product is arithmetic-bound (the ridge point is ~0.15 flop/byte
-// against 6.7 TB/s HBM) and everything else -- loads, index arithmetic --
-// hides behind the FMA pipe. What matters is (1) keeping every lane of every
-// DFMA busy (elements mapped densely onto lanes), (2) enough independent
-// accumulators per lane to cover the FMA latency, (3) reading each C block
-// once and writing it once. A team of W warps owns one C block: it walks the
-// block's products (ascending k, as stack generation ordered them; with W > 1
-// warp w takes products w, w+W, ... and the partial sums are added in warp
-// order through shared memory), keeps the C block in registers, and writes
-// alpha*acc + beta*C_old once -- no atomics on C. Work is handed out by an
-// atomic counter over a (possibly variant-filtered) list of C blocks
-// (persistent grid).
+// (DFMA and DMMA alike), i.e. under two FP64 FMAs per clock per SM, so a block
+// product is arithmetic-bound once its operands are on chip (the ridge point
+// is ~0.15 flop/byte against 6.7 TB/s HBM). What matters is (1) keeping every
+// lane of every DFMA busy (elements mapped densely onto lanes), (2) enough
+// independent accumulators and resident warps to cover latency, (3) never
+// waiting on a chain of dependent index loads per product, (4) reading each C
+// block once and writing it once.
+//
+// A team of W warps owns one C block: it walks the block's products (ascending
+// k, as stack generation ordered them; with W > 1 warp w takes products w,
+// w+W, ... and the partial sums are added in warp order through shared
+// memory), keeps the C block in registers, and writes alpha*acc + beta*C_old
+// once -- no atomics on C. Each warp fetches the index data of 32 of its
+// products at once (one lane per product) and broadcasts it with shuffles.
+// C blocks are grouped by (variant, elements per lane) so that small blocks
+// run in a low-register instance with many resident warps; work is handed out
+// by an atomic counter per group (persistent grid).
 #include <vector>
 
 #include "internal.cuh"
@@ -37,6 +41,13 @@ struct VariantShape {
     int cta_threads;
 };
 constexpr VariantShape kVariants[SMM_NUM_VARIANTS] = {{1, 256}, {1, 128}, {2, 256}, {4, 256}};
+constexpr int NQ = 6;                         // elements-per-lane classes 1, 2, 4, 8, 16, 32
+constexpr int kQ[NQ] = {1, 2, 4, 8, 16, 32};
+
+__host__ __device__ inline int q_class(int mn) {
+    const int q = (mn + 31) / 32;
+    return q <= 1 ? 0 : q <= 2 ? 1 : q <= 4 ? 2 : q <= 8 ? 3 : q <= 16 ? 4 : 5;
+}
 
 // barrier of one team of W warps (named barrier team+1; teams work on different
 // C blocks, so a CTA-wide barrier would couple them)
@@ -52,26 +63,41 @@ __device__ __forceinline__ void team_sync(int team) {
 // one team per C block; each lane holds up to Q elements e = lane + 32*q,
 // r = e % m, c = e / m (column-major order within the block)
 template <int Q, int TA, int TB, int W>
-__global__ void __launch_bounds__(256) k_smm_fp64(SmmArgs g, const int* __restrict__ list, int64_t nlist) {
+__global__ void __launch_bounds__(256) k_smm_fp64(SmmArgs g, const uint32_t* __restrict__ list, int64_t nlist,
+                                                        int chunk) {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int team = warp / W, tw = warp % W;        // team in CTA, warp in team
     __shared__ int s_cb[8];
     extern __shared__ double s_red[];                 // [teams][W-1][Q][32] partial sums
     for (;;) {
-        if (tw == 0 && lane == 0) s_cb[team] = (int)atomicAdd(g.counter, 1ULL);
+        // a team takes 32 consecutive C blocks at a time; lane t fetches block
+        // t's index data in parallel, then the blocks are processed in order
+        if (tw == 0 && lane == 0) s_cb[team] = (int)atomicAdd(g.counter, (unsigned long long)chunk);
         team_sync<W>(team);
-        const int64_t li = s_cb[team];
+        const int64_t lbase = s_cb[team];
         team_sync<W>(team);
-        if (li >= nlist) break;
-        const int64_t cb = list ? list[li] : li;
-        const int i = g.c_row[cb], j = g.c_col[cb];
-        const int m = g.rsC[i], n = g.csC[j];
+        if (lbase >= nlist) break;
+        const int nbat = (int)min((int64_t)chunk, nlist - lbase);
+        int my_m = 1, my_n = 1;
+        long long my_p0 = 0, my_p1 = 0, my_coff = 0, my_old = -1;
+        if (lane < nbat) {
+            const int64_t cbl = list ? (int64_t)list[lbase + lane] : lbase + lane;
+            my_m = g.rsC[g.c_row[cbl]];
+            my_n = g.csC[g.c_col[cbl]];
+            my_p0 = g.c_pstart[cbl];
+            my_p1 = g.c_pstart[cbl + 1];
+            my_coff = g.c_off[cbl];
+            const int o = g.c_old ? g.c_old[cbl] : -1;
+            my_old = (o >= 0) ? (long long)g.Cold_off[o] : -1;
+        }
+        for (int bt = 0; bt < nbat; bt++) {
+        const int m = __shfl_sync(0xffffffffu, my_m, bt), n = __shfl_sync(0xffffffffu, my_n, bt);
         const int mn = m * n;
-        const int64_t p0 = g.c_pstart[cb], p1 = g.c_pstart[cb + 1];
-        double* cout = g.Cd + g.c_off[cb];
-        const int old = g.c_old ? g.c_old[cb] : -1;
-        const double* cold = (old >= 0) ? g.Cold + g.Cold_off[old] : nullptr;
+        const int64_t p0 = __shfl_sync(0xffffffffu, my_p0, bt), p1 = __shfl_sync(0xffffffffu, my_p1, bt);
+        double* cout = g.Cd + __shfl_sync(0xffffffffu, my_coff, bt);
+        const long long old_off = __shfl_sync(0xffffffffu, my_old, bt);
+        const double* cold = (old_off >= 0) ? g.Cold + old_off : nullptr;
         for (int e0 = 0; e0 < mn; e0 += 32 * Q) {
             const int nq = min(Q, (mn - e0 + 31) >> 5);
             double acc[Q];
@@ -84,26 +110,40 @@ __global__ void __launch_bounds__(256) k_smm_fp64(SmmArgs g, const int* __restri
                 ro[q] = e % m;
                 co[q] = e / m;
             }
-            for (int64_t p = p0 + tw; p < p1; p += W) {
-                const int2 pr = g.prod[p];
-                const int64_t ao = g.A.off[pr.x];
-                const int kk = (int)((g.A.off[pr.x + 1] - ao) / m);
-                const double* __restrict__ a = g.A.data + ao;
-                const double* __restrict__ b = g.B.data + g.B.off[pr.y];
-                int aidx[Q], bidx[Q];
-#pragma unroll
-                for (int q = 0; q < Q; q++) {
-                    aidx[q] = TA ? ro[q] * kk : ro[q];
-                    bidx[q] = TB ? co[q] : co[q] * kk;
+            // this warp's products p0 + tw + W*t, 32 at a time: lane t fetches
+            // product t's operand offsets and inner size, then they are broadcast
+            for (int64_t pb = p0 + tw; pb < p1; pb += (int64_t)32 * W) {
+                const int64_t pj = pb + (int64_t)lane * W;
+                long long my_ao = 0, my_bo = 0;
+                int my_kk = 0;
+                if (pj < p1) {
+                    const int2 pr = g.prod[pj];
+                    my_ao = g.A.off[pr.x];
+                    my_kk = (int)((g.A.off[pr.x + 1] - my_ao) / m);
+                    my_bo = g.B.off[pr.y];
                 }
-                const int astep = TA ? 1 : m;
-                const int bstep = TB ? n : 1;
-                for (int l = 0; l < kk; l++) {
+                const int nb = (int)min((int64_t)32, (p1 - pb + W - 1) / W);
+                for (int t = 0; t < nb; t++) {
+                    const long long ao = __shfl_sync(0xffffffffu, my_ao, t);
+                    const long long bo = __shfl_sync(0xffffffffu, my_bo, t);
+                    const int kk = __shfl_sync(0xffffffffu, my_kk, t);
+                    const double* __restrict__ a = g.A.data + ao;
+                    const double* __restrict__ b = g.B.data + bo;
+                    int aidx[Q], bidx[Q];
 #pragma unroll
                     for (int q = 0; q < Q; q++) {
-                        if (q < nq) acc[q] = fma(__ldg(a + aidx[q]), __ldg(b + bidx[q]), acc[q]);
-                        aidx[q] += astep;
-                        bidx[q] += bstep;
+                        aidx[q] = TA ? ro[q] * kk : ro[q];
+                        bidx[q] = TB ? co[q] : co[q] * kk;
+                    }
+                    const int astep = TA ? 1 : m;
+                    const int bstep = TB ? n : 1;
+                    for (int l = 0; l < kk; l++) {
+#pragma unroll
+                        for (int q = 0; q < Q; q++) {
+                            if (q < nq) acc[q] = fma(__ldg(a + aidx[q]), __ldg(b + bidx[q]), acc[q]);
+                            aidx[q] += astep;
+                            bidx[q] += bstep;
+                        }
                     }
                 }
             }
@@ -134,16 +174,20 @@ __global__ void __launch_bounds__(256) k_smm_fp64(SmmArgs g, const int* __restri
                 }
             }
         }
+        }   // blocks of the batch
     }
 }
 
 template <int Q, int W>
-int launch_qw(const SmmArgs& g, const int* list, int64_t nlist, int threads) {
+int launch_qw(const SmmArgs& g, const uint32_t* list, int64_t nlist, int threads) {
     cudaStream_t st = ctx().stream;
     const int teams_per_cta = threads / (32 * W);
     int grid = ctx().num_sms * (2048 / threads);
     if ((int64_t)grid * teams_per_cta > nlist) grid = (int)cdiv(nlist, teams_per_cta);
     if (grid < 1) return DBCSR_OK;
+    // C blocks per work grab: up to 32, but at least ~4 grabs per team so
+    // that few heavy blocks still spread over all teams
+    const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(32, nlist / ((int64_t)grid * teams_per_cta * 4)));
     const size_t red = (W > 1) ? (size_t)teams_per_cta * (W - 1) * Q * 32 * sizeof(double) : 0;
     const int ta = g.A.trans, tb = g.B.trans;
 #define DB_LAUNCH_SMM(TA_, TB_)                                                                             \
@@ -151,7 +195,7 @@ int launch_qw(const SmmArgs& g, const int* list, int64_t nlist, int threads) {
         if (red > 0)                                                                                       \
             DB_CUDA(cudaFuncSetAttribute(k_smm_fp64<Q, TA_, TB_, W>,                                       \
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)red));          \
-        k_smm_fp64<Q, TA_, TB_, W><<<grid, threads, red, st>>>(g, list, nlist);                             \
+        k_smm_fp64<Q, TA_, TB_, W><<<grid, threads, red, st>>>(g, list, nlist, chunk);                           \
     } while (0)
     if (!ta && !tb) DB_LAUNCH_SMM(0, 0);
     else if (ta && !tb) DB_LAUNCH_SMM(1, 0);
@@ -163,69 +207,49 @@ int launch_qw(const SmmArgs& g, const int* list, int64_t nlist, int threads) {
 }
 
 template <int W>
-int launch_w(const SmmArgs& g, const int* list, int64_t nlist, int threads, int max_mn) {
-    const int q = (max_mn + 31) / 32;
-    if (q <= 1) return launch_qw<1, W>(g, list, nlist, threads);
-    if (q <= 2) return launch_qw<2, W>(g, list, nlist, threads);
-    if (q <= 4) return launch_qw<4, W>(g, list, nlist, threads);
-    if (q <= 8) return launch_qw<8, W>(g, list, nlist, threads);
-    if (q <= 16) return launch_qw<16, W>(g, list, nlist, threads);
-    return launch_qw<32, W>(g, list, nlist, threads);   // larger blocks loop over element chunks
-}
-
-int launch_variant(const SmmArgs& g, int variant, const int* list, int64_t nlist, int max_mn) {
-    const VariantShape v = kVariants[variant];
-    switch (v.team_warps) {
-        case 1: return launch_w<1>(g, list, nlist, v.cta_threads, max_mn);
-        case 2: return launch_w<2>(g, list, nlist, v.cta_threads, max_mn);
-        default: return launch_w<4>(g, list, nlist, v.cta_threads, max_mn);
+int launch_w(const SmmArgs& g, const uint32_t* list, int64_t nlist, int threads, int qidx) {
+    switch (qidx) {
+        case 0: return launch_qw<1, W>(g, list, nlist, threads);
+        case 1: return launch_qw<2, W>(g, list, nlist, threads);
+        case 2: return launch_qw<4, W>(g, list, nlist, threads);
+        case 3: return launch_qw<8, W>(g, list, nlist, threads);
+        case 4: return launch_qw<16, W>(g, list, nlist, threads);
+        default: return launch_qw<32, W>(g, list, nlist, threads);   // larger blocks loop over chunks
     }
 }
 
-// variant of every C block from the (m, n) table; counts per variant
+int launch_group(const SmmArgs& g, int variant, int qidx, const uint32_t* list, int64_t nlist) {
+    const VariantShape v = kVariants[variant];
+    switch (v.team_warps) {
+        case 1: return launch_w<1>(g, list, nlist, v.cta_threads, qidx);
+        case 2: return launch_w<2>(g, list, nlist, v.cta_threads, qidx);
+        default: return launch_w<4>(g, list, nlist, v.cta_threads, qidx);
+    }
+}
+
+// group key of every C block: variant * NQ + elements-per-lane class
 __global__ void k_classify(int64_t nC, const int* __restrict__ c_row, const int* __restrict__ c_col,
-                           const int* __restrict__ rsC, const int* __restrict__ csC,
-                           const signed char* __restrict__ table, int tdim, int dflt, int* __restrict__ var,
-                           int* __restrict__ counts) {
+                           const int64_t* __restrict__ c_pstart, const int* __restrict__ rsC,
+                           const int* __restrict__ csC,
+                           const signed char* __restrict__ table, int tdim, int forced, uint32_t* __restrict__ key,
+                           uint32_t* __restrict__ idx, int* __restrict__ counts) {
     const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (b >= nC) return;
     const int m = rsC[c_row[b]], n = csC[c_col[b]];
-    int v = dflt;
-    if (m < tdim && n < tdim) {
+    int v = forced >= 0 ? forced : 0;
+    if (forced < 0 && table && m < tdim && n < tdim) {
         const int t = table[m * tdim + n];
         if (t >= 0) v = t;
+        // a team only pays off with at least two products per warp; a C block
+        // with fewer runs on one warp (its team-mates would wait at the barrier)
+        const int64_t nprod = c_pstart[b + 1] - c_pstart[b];
+        const int team_warps = (v == 2) ? 2 : (v == 3) ? 4 : 1;   // kVariants[v].team_warps
+        if (nprod < 2 * team_warps) v = 0;
     }
-    var[b] = v;
-    atomicAdd(&counts[v], 1);
-}
-
-// stable per-variant lists (one CTA, ordered scan over the blocks)
-__global__ void k_partition(int64_t nC, const int* __restrict__ var, const int* __restrict__ start,
-                            int* __restrict__ list) {
-    __shared__ int cursor[SMM_NUM_VARIANTS];
-    if (threadIdx.x < SMM_NUM_VARIANTS) cursor[threadIdx.x] = start[threadIdx.x];
-    __syncthreads();
-    for (int64_t base = 0; base < nC; base += blockDim.x) {
-        const int64_t b = base + threadIdx.x;
-        const int v = b < nC ? var[b] : -1;
-        for (int w = 0; w < SMM_NUM_VARIANTS; w++) {
-            const unsigned mask = __ballot_sync(0xffffffffu, v == w);
-            __shared__ int warp_cnt[32];
-            const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-            if (lane == 0) warp_cnt[wid] = __popc(mask);
-            __syncthreads();
-            int before = 0;
-            for (int q = 0; q < wid; q++) before += warp_cnt[q];
-            if (v == w) list[cursor[w] + before + __popc(mask & ((1u << lane) - 1u))] = (int)b;
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                int tot = 0;
-                for (int q = 0; q < (int)(blockDim.x >> 5); q++) tot += warp_cnt[q];
-                cursor[w] += tot;
-            }
-            __syncthreads();
-        }
-    }
+    const int k = v * NQ + q_class(m * n);
+    key[b] = (uint32_t)k;
+    idx[b] = (uint32_t)b;
+    atomicAdd(&counts[k], 1);
 }
 
 // (m, n) -> variant table set by dbcsr_set_tuning; -1 = default
@@ -248,51 +272,55 @@ int smm_set_table(const int* m, const int* n, const int* variant, int count) {
     return DBCSR_OK;
 }
 
-int smm_fp64_generic(const SmmArgs& g, int max_mn) { return launch_variant(g, 0, nullptr, g.nC, max_mn); }
+int smm_fp64_generic(const SmmArgs& g, int max_mn) {
+    if (g.nC == 0) return DBCSR_OK;
+    return launch_group(g, 0, q_class(max_mn), nullptr, g.nC);
+}
 
-// kernel: 0 = tuned table (default variant 0 for untuned shapes), v >= 1 = force variant v-1
+// kernel: 0 = tuned table (variant 0 for untuned shapes), v >= 1 = force variant v-1.
+// C blocks are grouped by (variant, elements-per-lane class); one launch per group.
 int smm_fp64_dispatch(const SmmArgs& g, int max_mn, int kernel) {
     if (g.nC == 0) return DBCSR_OK;
     if (kernel < 0 || kernel > SMM_NUM_VARIANTS) return fail(DBCSR_ERR_ARG, "unknown stack kernel variant");
-    if (kernel >= 1 || !g_table_used) return launch_variant(g, kernel >= 1 ? kernel - 1 : 0, nullptr, g.nC, max_mn);
+    if (g.nC >= INT32_MAX) return fail(DBCSR_ERR_OVERFLOW, "stack kernels: too many C blocks");
     cudaStream_t st = ctx().stream;
+    constexpr int NK = SMM_NUM_VARIANTS * NQ;
+    const bool use_table = kernel == 0 && g_table_used;
     DBuf<signed char> table;
-    DBuf<int> var, counts, list;
-    DB_TRY(table.alloc(TDIM * TDIM));
-    DB_TRY(var.alloc(g.nC));
-    DB_TRY(counts.alloc(SMM_NUM_VARIANTS));
-    DB_TRY(list.alloc(g.nC));
-    DB_CUDA(cudaMemcpyAsync(table.p, g_table.data(), TDIM * TDIM, cudaMemcpyHostToDevice, st));
-    DB_CUDA(cudaMemsetAsync(counts.p, 0, sizeof(int) * SMM_NUM_VARIANTS, st));
-    k_classify<<<(unsigned)cdiv(g.nC, 256), 256, 0, st>>>(g.nC, g.c_row, g.c_col, g.rsC, g.csC, table.p, TDIM, 0,
-                                                          var.p, counts.p);
+    DBuf<uint32_t> key, idx;
+    DBuf<int> counts;
+    if (use_table) {
+        DB_TRY(table.alloc(TDIM * TDIM));
+        DB_CUDA(cudaMemcpyAsync(table.p, g_table.data(), TDIM * TDIM, cudaMemcpyHostToDevice, st));
+    }
+    DB_TRY(key.alloc(g.nC));
+    DB_TRY(idx.alloc(g.nC));
+    DB_TRY(counts.alloc(NK));
+    DB_CUDA(cudaMemsetAsync(counts.p, 0, sizeof(int) * NK, st));
+    k_classify<<<(unsigned)cdiv(g.nC, 256), 256, 0, st>>>(g.nC, g.c_row, g.c_col, g.c_pstart, g.rsC, g.csC,
+                                                          use_table ? table.p : nullptr, TDIM,
+                                                          kernel >= 1 ? kernel - 1 : -1, key.p, idx.p, counts.p);
     DB_KCHECK();
-    int h_counts[SMM_NUM_VARIANTS];
-    DB_CUDA(cudaMemcpyAsync(h_counts, counts.p, sizeof(h_counts), cudaMemcpyDeviceToHost, st));
+    std::vector<int> h_counts(NK);
+    DB_CUDA(cudaMemcpyAsync(h_counts.data(), counts.p, sizeof(int) * NK, cudaMemcpyDeviceToHost, st));
     DB_CUDA(cudaStreamSynchronize(st));
     int used = 0, only = 0;
-    for (int v = 0; v < SMM_NUM_VARIANTS; v++)
-        if (h_counts[v]) { used++; only = v; }
-    if (used <= 1) return launch_variant(g, only, nullptr, g.nC, max_mn);
-    int h_start[SMM_NUM_VARIANTS];
-    int run = 0;
-    for (int v = 0; v < SMM_NUM_VARIANTS; v++) { h_start[v] = run; run += h_counts[v]; }
-    DBuf<int> start;
-    DB_TRY(start.alloc(SMM_NUM_VARIANTS));
-    DB_CUDA(cudaMemcpyAsync(start.p, h_start, sizeof(h_start), cudaMemcpyHostToDevice, st));
-    k_partition<<<1, 1024, 0, st>>>(g.nC, var.p, start.p, list.p);
-    DB_KCHECK();
-    // each variant's launch works through its own list with its own counter
+    for (int k = 0; k < NK; k++)
+        if (h_counts[k]) { used++; only = k; }
+    if (used <= 1) return launch_group(g, only / NQ, only % NQ, nullptr, g.nC);
+    // stable sort of the C blocks by group: each group's blocks keep CSR order
+    DB_TRY(radix_sort_u32(key.p, idx.p, g.nC, 8));
     DBuf<unsigned long long> ctr;
-    DB_TRY(ctr.alloc(SMM_NUM_VARIANTS));
-    DB_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(unsigned long long) * SMM_NUM_VARIANTS, st));
-    for (int v = 0; v < SMM_NUM_VARIANTS; v++) {
-        if (!h_counts[v]) continue;
-        SmmArgs gv = g;
-        gv.counter = ctr.p + v;
-        DB_TRY(launch_variant(gv, v, list.p + h_start[v], h_counts[v], max_mn));
+    DB_TRY(ctr.alloc(NK));
+    DB_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(unsigned long long) * NK, st));
+    int64_t start = 0;
+    for (int k = 0; k < NK; k++) {
+        if (!h_counts[k]) continue;
+        SmmArgs gk = g;
+        gk.counter = ctr.p + k;
+        DB_TRY(launch_group(gk, k / NQ, k % NQ, idx.p + start, h_counts[k]));
+        start += h_counts[k];
     }
-    DB_CUDA(cudaStreamSynchronize(st));   // h_start / h_counts above are stack memory
     return DBCSR_OK;
 }
 

@@ -19,6 +19,8 @@ struct OzParams {
     int64_t units;        // tiles_m * tiles_n * ksegs * s
     double* ws;           // slices: [s][ksegs][N][M] exact level sums (column-major M x N)
     int64_t ws_stride;    // M * N
+    int* ws_i32;          // slices, 256-wide kernel: [s][ksegs][M][ldws] exact int32 level sums (row-major)
+    int64_t ldws;         // multiple of 256, >= N
     double* C;            // tf32: output, column-major
     int64_t ldc;
     double alpha, beta;
@@ -37,5 +39,11 @@ int oz_gemm_launch_on(const CUtensorMap& tmA, const CUtensorMap& tmB, const OzPa
                       int num_sms);
 // TF32 GEMM writing C directly
 int tf32_gemm_launch(const CUtensorMap& tmA, const CUtensorMap& tmB, const OzParams& p, int cluster_m);
+
+// 128 x 256 tiles (tc_gemm256.cu): usable when its compiled register budget
+// matches its warp-group register split; tmB's box then holds 256 rows.
+bool tc256_usable();
+int oz_gemm256_launch(const CUtensorMap& tmA, const CUtensorMap& tmB, const OzParams& p);   // writes ws_i32
+int tf32_gemm256_launch(const CUtensorMap& tmA, const CUtensorMap& tmB, const OzParams& p);
 
 }  // namespace dbcsr

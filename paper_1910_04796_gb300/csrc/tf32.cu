@@ -64,8 +64,9 @@ int dgemm_tf32(int64_t M, int64_t N, int64_t K, double alpha, const double* A, i
     DB_KCHECK();
     CUtensorMap tmA, tmB;
     DB_TRY(make_slice_tmap(&tmA, AT.p, ldk, M, 1, 128, 4));
-    const int cm = tc_cluster_m(M);
-    DB_TRY(make_slice_tmap(&tmB, BT.p, ldk, N, 1, 128 / cm, 4));
+    const bool wide = N >= 256 && tc256_usable();
+    const int cm = wide ? 1 : tc_cluster_m(M);
+    DB_TRY(make_slice_tmap(&tmB, BT.p, ldk, N, 1, wide ? 256 : 128 / cm, 4));
     OzParams p{};
     p.M = (int)M;
     p.N = (int)N;
@@ -85,13 +86,14 @@ int dgemm_tf32(int64_t M, int64_t N, int64_t K, double alpha, const double* A, i
     p.err = ctx().d_flags;
     DB_CUDA(cudaMemsetAsync(p.err, 0, sizeof(int), st));
     timer_kernel_begin();
-    DB_TRY(tf32_gemm_launch(tmA, tmB, p, cm));
+    if (wide) DB_TRY(tf32_gemm256_launch(tmA, tmB, p));
+    else DB_TRY(tf32_gemm_launch(tmA, tmB, p, cm));
     timer_kernel_end();
     int h_err = 0;
     DB_CUDA(cudaMemcpyAsync(&h_err, p.err, sizeof(int), cudaMemcpyDeviceToHost, st));
     DB_CUDA(cudaStreamSynchronize(st));
     if (h_err) return fail(DBCSR_ERR_TIMEOUT, "tf32 gemm: a tensor-core pipeline wait timed out");
-    if (main_flops) *main_flops = 2.0 * (double)(p.tiles_m * 128) * (double)(p.tiles_n * 128) * (double)ldk;
+    if (main_flops) *main_flops = 2.0 * (double)M * (double)N * (double)K;   // algorithmic, unpadded
     return DBCSR_OK;
 }
 
