@@ -437,10 +437,12 @@ int oracle_num_threads(void)
  *  3. Integer products, kept exactly: for each level d = t + u with
  *     2 <= d <= s+1 (the triangular truncation: pairs with t + u > s + 1 are
  *     dropped), G_d(i,j) = sum over t+u=d of sum_l sigmaA_t(i,l) sigmaB_u(l,j).
- *  4. Recombination in FP64, smallest level first:
- *     acc = 0; for d = s+1 down to 2: acc = acc + G_d * 2^(-7d)
- *     (each term exact, one rounding per sum).
- *  5. C(i,j) = alpha * (acc * 2^(e_i + f_j)) + beta * C(i,j).
+ *  4. Recombination, exact then rounded once: the integer
+ *     S = sum_{d=2}^{s+1} G_d * 2^(7(s+1-d)) is formed exactly (128-bit), and
+ *     acc = S * 2^(-7(s+1)) is S converted to FP64 with one rounding to
+ *     nearest (ties to even), scaled by an exact power of two.
+ *  5. C(i,j) = alpha * (acc * 2^(e_i + f_j)) + beta * C(i,j), where the
+ *     product by 2^(e_i + f_j - 7(s+1)) is one ldexp of the rounded S.
  * ------------------------------------------------------------------------- */
 static int frexp_exp(double mu)
 {
@@ -529,9 +531,9 @@ int oracle_ozaki_gemm(int64_t M, int64_t N, int64_t K, double alpha, const doubl
                     }
                 }
             for (int64_t j = 0; j < N; j++) {
-                double acc = 0.0;
-                for (int d = s + 1; d >= 2; d--) acc = acc + ldexp((double)G[(size_t)d * N + j], -7 * d);
-                double v = alpha * ldexp(acc, e_row[i] + f_col[j]);
+                __int128 S = 0;
+                for (int d = 2; d <= s + 1; d++) S += (__int128)G[(size_t)d * N + j] << (7 * (s + 1 - d));
+                double v = alpha * ldexp((double)S, e_row[i] + f_col[j] - 7 * (s + 1));
                 if (beta != 0.0) v = v + beta * C[i + j * ldc];
                 C[i + j * ldc] = v;
             }

@@ -17,6 +17,7 @@
 #include <mutex>
 
 #include "emul.cuh"
+#include "emul_common.cuh"
 #include "tc_gemm.cuh"
 
 namespace dbcsr {
@@ -154,13 +155,13 @@ __global__ void k_recombine(int64_t M, int64_t N, int s, int ksegs, const double
     const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (idx >= M * N) return;
     const int64_t i = idx % M, j = idx / M;
-    double acc = 0.0;
-    for (int d = s + 1; d >= 2; d--) {
-        double g = 0.0;   // exact: integer partial sums below 2^53
-        for (int k = 0; k < ksegs; k++) g += ws[((int64_t)(d - 2) * ksegs + k) * stride + idx];
-        acc = fma(g, ldexp(1.0, -7 * d), acc);   // g * 2^-7d is exact: one rounding
+    __int128 S = 0;   // exact sum of the level sums, each shifted to its weight
+    for (int d = 2; d <= s + 1; d++) {
+        long long g = 0;   // FP64 workspace entries are exact integers below 2^53
+        for (int k = 0; k < ksegs; k++) g += (long long)ws[((int64_t)(d - 2) * ksegs + k) * stride + idx];
+        S += (__int128)g << (7 * (s + 1 - d));
     }
-    double v = __dmul_rn(alpha, ldexp(acc, e[i] + f[j]));
+    double v = __dmul_rn(alpha, emul::round_i128_scaled(S, e[i] + f[j] - 7 * (s + 1)));
     if (beta != 0.0) v = __dadd_rn(v, __dmul_rn(beta, C[i + j * ldc]));
     C[i + j * ldc] = v;
 }
@@ -190,12 +191,13 @@ __global__ void __launch_bounds__(256) k_recombine_rm(int64_t M, int64_t N, int 
         const int64_t i = i0 + r, j = j0 + tx;
         double acc = 0.0;
         if (i < M && j < N) {
-            for (int d = s + 1; d >= 2; d--) {
+            __int128 S = 0;   // exact sum of the level sums, each shifted to its weight
+            for (int d = 2; d <= s + 1; d++) {
                 int64_t g = 0;   // exact: sum over K segments of int32 partial sums
                 for (int k = 0; k < ksegs; k++) g += ws[((int64_t)(d - 2) * ksegs + k) * lstride + i * ldws + j];
-                acc = fma((double)g, pow2(-7 * d), acc);
+                S += (__int128)g << (7 * (s + 1 - d));
             }
-            acc = scale2(acc, e[i] + f[j]);
+            acc = emul::round_i128_scaled(S, e[i] + f[j] - 7 * (s + 1));
         }
         tile[r][tx] = acc;
     }

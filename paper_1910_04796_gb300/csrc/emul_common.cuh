@@ -51,5 +51,45 @@ __device__ __forceinline__ unsigned long long abs_bits(double x) {
     return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
 }
 
+// Recombination of the level sums: S = sum_d G_d 2^(7(s+1-d)) is an exact
+// 128-bit integer; the result is S rounded once to FP64 (to nearest, ties to
+// even) and multiplied by 2^k exactly -- the same as ldexp((double)S, k).
+// Integer operations only, except ldexp outside the normal range.
+__device__ __forceinline__ double round_i128_scaled(__int128 S, int k) {
+    if (S == 0) return 0.0;
+    const bool neg = S < 0;
+    const unsigned __int128 a = neg ? (unsigned __int128)(-S) : (unsigned __int128)S;
+    const unsigned long long hi = (unsigned long long)(a >> 64), lo = (unsigned long long)a;
+    const int msb = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);   // leading one
+    unsigned long long mant;   // significand in [2^52, 2^53)
+    int ex;                    // |S| rounded = mant * 2^ex
+    if (msb <= 52) {
+        mant = lo << (52 - msb);
+        ex = msb - 52;
+    } else {
+        const int sh = msb - 52;
+        const unsigned __int128 q = a >> sh;
+        mant = (unsigned long long)q;
+        const unsigned __int128 rem = a - (q << sh);
+        const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
+        ex = sh;
+        if (rem > half || (rem == half && (mant & 1ull))) {
+            mant += 1;
+            if (mant >> 53) {   // carried into a new power of two
+                mant >>= 1;
+                ex += 1;
+            }
+        }
+    }
+    const int E = ex + k + 52;   // result = mant / 2^52 * 2^E
+    if (E >= -1022 && E <= 1023) {
+        const unsigned long long bits = ((unsigned long long)neg << 63) |
+                                        ((unsigned long long)(E + 1023) << 52) | (mant & 0xfffffffffffffull);
+        return __longlong_as_double((long long)bits);
+    }
+    const double r = ldexp((double)mant, ex);   // exact: |S| < 2^127
+    return ldexp(neg ? -r : r, k);
+}
+
 }  // namespace emul
 }  // namespace dbcsr

@@ -315,10 +315,11 @@ __global__ void __launch_bounds__(SE_THREADS) k_smm_emul(SeArgs a) {
                 const int row = wm * 16 + g + 8 * (r >> 1);
                 const int colm = wn * 16 + nt * 8 + 2 * q + (r & 1);
                 if (row < m && colm < n) {
-                    double v = 0.0;
+                    __int128 Sx = 0;   // exact sum of the level sums, each shifted to its weight
 #pragma unroll
-                    for (int d = S - 1; d >= 0; d--) v = fma((double)gi[d][nt][r], ldexp(1.0, -7 * (d + 2)), v);
-                    v = __dmul_rn(a.alpha, ldexp(v, a.e[rbase + row] + a.f[cbase + colm]));
+                    for (int d = 0; d < S; d++) Sx += (__int128)gi[d][nt][r] << (7 * (S - 1 - d));
+                    double v = __dmul_rn(
+                        a.alpha, emul::round_i128_scaled(Sx, a.e[rbase + row] + a.f[cbase + colm] - 7 * (S + 1)));
                     const int64_t eidx = (int64_t)colm * m + row;
                     if (cold) v = __dadd_rn(v, __dmul_rn(a.beta, cold[eidx]));
                     cout[eidx] = v;

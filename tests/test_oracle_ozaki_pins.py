@@ -141,3 +141,21 @@ def test_round_tf32_known_values():
     # the result has at most 11 significant bits
     m, _ = np.frexp(r)
     assert np.all(m * 2 ** 11 == np.round(m * 2 ** 11))
+
+
+@pytest.mark.parametrize("s", [3, 7, 8])
+def test_recombination_is_exact_sum_rounded_once(s):
+    # C = alpha * round(sum_d G_d 2^-7d) * 2^(e+f): with alpha = 1, beta = 0 each
+    # C(i,j) must be the correctly rounded value of the exact rational sum
+    # (Python's float(Fraction) rounds to nearest, ties to even)
+    rng = np.random.default_rng(57 + s)
+    M, K, N = 4, 40, 5
+    A = np.asfortranarray(rng.uniform(-1, 1, (M, K)) * 10.0 ** rng.uniform(-3, 3, (M, K)))
+    B = np.asfortranarray(rng.uniform(-1, 1, (K, N)) * 10.0 ** rng.uniform(-3, 3, (K, N)))
+    e, f = O.ozaki_exponents(A, B)
+    Cd, lv = O.ozaki_gemm(1.0, A, B, 0.0, np.zeros((M, N), order="F"), s=s, want_levels=True)
+    for i in range(M):
+        for j in range(N):
+            exact = sum(Fraction(int(lv[d - 2][i][j])) * Fraction(2) ** (-7 * d) for d in range(2, s + 2))
+            exact *= Fraction(2) ** (int(e[i]) + int(f[j]))
+            assert Cd[i, j] == float(exact)
