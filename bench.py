@@ -250,6 +250,8 @@ def main():
     ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "ozaki", "tf32"])
     ap.add_argument("--path", default="auto", choices=["auto", "stacks", "dense"])
     ap.add_argument("--slices", type=int, default=0)
+    ap.add_argument("--kernel", type=int, default=0,
+                    help="stack kernel choice passed to dbcsr_multiply (0 = automatic)")
     ap.add_argument("--ref-rows", type=int, default=48, help="C block rows per oracle sample")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -285,7 +287,7 @@ def main():
 
     def step(prec=precision, path=args.path, timing=False):
         dbcsr.multiply(w.transa, w.transb, w.alpha, A, B, w.beta, Cm, path=path, precision=prec,
-                       ozaki_slices=args.slices, timing=timing)
+                       ozaki_slices=args.slices, kernel=args.kernel, timing=timing)
 
     step()
     st = dbcsr.stats()
@@ -378,7 +380,7 @@ def main():
             else:
                 Ch = dbcsr.Matrix.create(rs, cs, np.zeros(0, np.int32), np.zeros(0, np.int32))
             dbcsr.multiply(w.transa, w.transb, w.alpha, Ah, Bh, w.beta, Ch, path=args.path, precision=precision,
-                           ozaki_slices=args.slices)
+                           ozaki_slices=args.slices, kernel=args.kernel)
             out = Ch.data()
             for m in (Ah, Bh, Ch):
                 m.release()

@@ -623,11 +623,7 @@ int multiply_stacks(bool ta, bool tb, double alpha, dbcsr_matrix_s* A, dbcsr_mat
         timer_kernel_end();
         g_stats.main_flops = g_stats.useful_flops;
     } else {
-        rc = smm_emulated(g, A, ta, B, tb, C, o, nullptr);
-        const int s = o.ozaki_slices > 0 ? o.ozaki_slices : 7;
-        auto r16 = [](int x) { return (double)((x + 15) & ~15); };
-        g_stats.main_flops = (double)P.nprod * (s * (s + 1) / 2) * 2.0 * r16(C->max_rs) * r16(C->max_cs) *
-                             r16(ta ? A->max_rs : A->max_cs);
+        rc = smm_emulated(g, A, ta, B, tb, C, o, P.nprod, &g_stats.main_flops);
     }
     mark(2);
     if (rc) { dfree(data, (size_t)(P.nelem ? P.nelem : 1)); return rc; }

@@ -73,6 +73,15 @@ __device__ __forceinline__ void tma_load_3d_multicast(void* dst, const CUtensorM
         "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar)), "h"(cta_mask)
         : "memory");
 }
+// untiled bulk copy global -> shared (16-byte aligned addresses, size a
+// multiple of 16), completing `bytes` on the mbarrier
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
 __device__ __forceinline__ uint32_t cluster_ctarank() {
     uint32_t r;
     asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
@@ -184,6 +193,19 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(const void* p) {
     d |= (uint64_t)1 << 46;                        // descriptor version [46,48)
     d |= (uint64_t)2 << 61;                        // layout: 128-byte swizzle [61,64)
     return d;
+}
+
+// Shared-memory matrix descriptor for a K-major operand without swizzle:
+// 8-row x 16-byte core matrices, `lbo` bytes between core matrices adjacent
+// in K, `sbo` bytes between 8-row groups.
+__device__ __forceinline__ uint64_t smem_desc_kmajor(const void* p, uint32_t lbo, uint32_t sbo) {
+    const uint32_t a = smem_u32(p);
+    uint64_t d = 0;
+    d |= (uint64_t)((a & 0x3FFFFu) >> 4);          // start address  [0,14)
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;    // leading byte offset [16,30)
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;    // stride byte offset [32,46)
+    d |= (uint64_t)1 << 46;                         // descriptor version [46,48)
+    return d;                                       // layout 0: no swizzle [61,64)
 }
 
 // Instruction descriptor, kind::f16 / kind::tf32: D fp32, A/B format

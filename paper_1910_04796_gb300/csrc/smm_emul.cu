@@ -24,6 +24,7 @@
 #include "emul_common.cuh"
 #include "internal.cuh"
 #include "smm.cuh"
+#include "smm_emul.cuh"
 
 namespace dbcsr {
 
@@ -34,32 +35,6 @@ constexpr int SE_MAXB = 32;    // largest block edge on this path
 constexpr int SE_RS = 40;      // shared-memory row stride (bf16): 32 + 8, conflict-free fragments
 
 __host__ __device__ inline int ru16(int x) { return (x + 15) & ~15; }
-
-// One matrix seen through op(): stored block b, element (x, l) of its op()
-// "row-like" view is data[off[b] + x*xs + l*ls]: x indexes op(A)'s rows (or
-// op(B)'s columns), l the inner dimension.
-struct SliceGeom {
-    const int* row_of;
-    const int* col;
-    const int64_t* off;
-    const double* data;
-    const int* rs;          // stored block row sizes
-    const int* cs;          // stored block column sizes
-    const int64_t* roff;    // stored element row offsets
-    const int64_t* coff;    // stored element column offsets
-    int64_t nblks;
-    int x_is_row;           // x runs over the stored rows (else stored columns)
-};
-
-__device__ __forceinline__ void geom_block(const SliceGeom& G, int64_t b, int& X, int& L, int& xs, int& ls,
-                                           int64_t& xbase) {
-    const int sr = G.rs[G.row_of[b]], sc = G.cs[G.col[b]];
-    if (G.x_is_row) {
-        X = sr; L = sc; xs = 1; ls = sr; xbase = G.roff[G.row_of[b]];
-    } else {
-        X = sc; L = sr; xs = sr; ls = 1; xbase = G.coff[G.col[b]];
-    }
-}
 
 // max |x| over each op() line: warp per stored block, lane per line
 __global__ void k_se_linemax(SliceGeom G, unsigned long long* __restrict__ out) {
@@ -346,8 +321,7 @@ int launch_se(const SeArgs& a, int grid) {
 int slices_of(dbcsr_matrix_s* M, bool x_is_row, const int* ex, int s, DBuf<int64_t>& soff, int64_t* total,
               DBuf<__nv_bfloat16>& S) {
     cudaStream_t st = ctx().stream;
-    SliceGeom G{M->d_row_of, M->d_col, M->d_off, M->d_data, M->d_rs, M->d_cs, M->d_roff, M->d_coff, M->nblks,
-                x_is_row ? 1 : 0};
+    const SliceGeom G = slice_geom(M, x_is_row);
     DB_TRY(soff.alloc(M->nblks + 1));
     if (M->nblks > 0) {
         k_se_slice_sizes<<<(unsigned)cdiv(M->nblks, 256), 256, 0, st>>>(G, soff.p);
@@ -370,8 +344,7 @@ int slices_of(dbcsr_matrix_s* M, bool x_is_row, const int* ex, int s, DBuf<int64
 
 int line_exponents(dbcsr_matrix_s* M, bool x_is_row, int64_t nlines, DBuf<int>& ex) {
     cudaStream_t st = ctx().stream;
-    SliceGeom G{M->d_row_of, M->d_col, M->d_off, M->d_data, M->d_rs, M->d_cs, M->d_roff, M->d_coff, M->nblks,
-                x_is_row ? 1 : 0};
+    const SliceGeom G = slice_geom(M, x_is_row);
     DBuf<unsigned long long> bits;
     DB_TRY(bits.alloc(nlines ? nlines : 1));
     DB_CUDA(cudaMemsetAsync(bits.p, 0, sizeof(unsigned long long) * (nlines ? nlines : 1), st));
@@ -391,7 +364,7 @@ int line_exponents(dbcsr_matrix_s* M, bool x_is_row, int64_t nlines, DBuf<int>& 
 }  // namespace
 
 int smm_emulated(const SmmArgs& g, dbcsr_matrix_s* A, bool ta, dbcsr_matrix_s* B, bool tb, dbcsr_matrix_s* C,
-                 const dbcsr_opts& o, double* main_flops) {
+                 const dbcsr_opts& o, int64_t nprod, double* main_flops) {
     if (o.precision != DBCSR_PREC_OZAKI)
         return fail(DBCSR_ERR_ARG, "the stack path runs in FP64 or emulated FP64; TF32 needs the dense path");
     const int s = o.ozaki_slices > 0 ? o.ozaki_slices : 7;
@@ -420,6 +393,15 @@ int smm_emulated(const SmmArgs& g, dbcsr_matrix_s* A, bool ta, dbcsr_matrix_s* B
     DBuf<int> e, f;
     DB_TRY(line_exponents(A, !ta, Mop, e));
     DB_TRY(line_exponents(B, tb, Nop, f));
+    // kernel: 0 = tcgen05 when every block edge is at least 24 (padding to
+    // 32 x 32 costs at most 2.4x), else mma.sync; 1 = mma.sync; 2 = tcgen05
+    int kmin = 1 << 30;
+    for (const std::vector<int>* v : {&A->h_rs, &A->h_cs, &B->h_rs, &B->h_cs})
+        for (int x : *v) kmin = std::min(kmin, x);
+    const bool tc_ok = smm_emul_tc_usable();
+    if (o.kernel == 2 && !tc_ok) return fail(DBCSR_ERR_STATE, "tcgen05 emulated stack kernel unavailable");
+    if (o.kernel == 2 || (o.kernel == 0 && kmin >= 24 && tc_ok))
+        return smm_emul_tc(g, A, ta, B, tb, C, e.p, f.p, s, nprod, main_flops);
     DBuf<int64_t> soffA, soffB;
     DBuf<__nv_bfloat16> SA, SB;
     int64_t totA = 0, totB = 0;
@@ -469,10 +451,8 @@ int smm_emulated(const SmmArgs& g, dbcsr_matrix_s* A, bool ta, dbcsr_matrix_s* B
     }
     timer_kernel_end();
     if (rc) return rc;
-    if (main_flops) {
-        // MMA work issued: per product, 2 * 16 * 16 * kp per quadrant pair (t,u), padded shapes
-        *main_flops = 0.0;   // filled by the caller from the product count (see api)
-    }
+    if (main_flops)   // MMA work issued: every pair t + u <= s + 1 on shapes padded to 16
+        *main_flops = (double)nprod * (s * (s + 1) / 2) * 2.0 * ru16(C->max_rs) * ru16(C->max_cs) * kp;
     return DBCSR_OK;
 }
 

@@ -3,7 +3,9 @@ the tensor cores, no densification).
 
 The level sums are exact integers, so the result must equal, bit for bit, the
 oracle's emulation of the densified operands; and it must meet 1e-12 against
-the plain FP64 oracle.
+the plain FP64 oracle. Both kernels are checked: kernel=1 (mma.sync, blocks
+padded to 16) and kernel=2 (tcgen05 with TMEM accumulators, blocks padded to
+32 x 32, products in chunks of 32 per C block).
 """
 import numpy as np
 import pytest
@@ -27,37 +29,68 @@ def emul_ref(ta, tb, A, B, Cm, alpha, beta, s):
     return synth.BlockSparse(pat.row_sizes, pat.col_sizes, pat.blk_row, pat.blk_col, data), Ad, Bd
 
 
-@pytest.mark.parametrize("s", [7, 3, 8])
-def test_precision_sparse_small_bit_exact(s):
+KERNELS = [1, 2]
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("s", [7, 3, 8, 1, 5])
+def test_precision_sparse_small_bit_exact(s, kernel):
     w = synth.workload_precision_sparse(seed=5, nblk=24, occ=0.15)
-    got, st = gpu_multiply("N", "N", 1.0, w.A, w.B, 0.0, path="stacks", precision="ozaki", ozaki_slices=s)
+    got, st = gpu_multiply("N", "N", 1.0, w.A, w.B, 0.0, path="stacks", precision="ozaki", ozaki_slices=s,
+                           kernel=kernel)
     ref, Ad, Bd = emul_ref("N", "N", w.A, w.B, None, 1.0, 0.0, s)
     assert_same_pattern(got, ref)
     assert np.array_equal(got.data, ref.data)
     assert st["path"] == dbcsr.PATH_STACKS
 
 
+@pytest.mark.parametrize("kernel", KERNELS)
 @pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("N", "T"), ("T", "T")])
-def test_uneven_blocks_transposes_beta(ta, tb):
+def test_uneven_blocks_transposes_beta(ta, tb, kernel):
     rng = np.random.default_rng(600)
     A, B, Cm = synth.random_small(rng, 9, 8, 10, p=0.4, sizes=(5, 13, 23, 26, 32), with_c=True, c_p=0.4)
     As = synth.transpose_blocks(A) if ta == "T" else A
     Bs = synth.transpose_blocks(B) if tb == "T" else B
-    got, _ = gpu_multiply(ta, tb, 0.5, As, Bs, 2.0, Cm, path="stacks", precision="ozaki")
+    got, _ = gpu_multiply(ta, tb, 0.5, As, Bs, 2.0, Cm, path="stacks", precision="ozaki", kernel=kernel)
     ref, _, _ = emul_ref(ta, tb, As, Bs, Cm, 0.5, 2.0, 7)
     assert_same_pattern(got, ref)
     assert np.array_equal(got.data, ref.data)
 
 
-def test_emulated_stacks_meet_1e12_and_integer_exact():
+@pytest.mark.parametrize("kernel", KERNELS)
+@pytest.mark.parametrize("nk", [32, 33, 70])
+def test_long_product_lists_chunked(nk, kernel):
+    # one C block row x one C block column, nk products per C block: the
+    # tcgen05 kernel's fp32 accumulators are flushed every 32 products
+    rng = np.random.default_rng(630 + nk)
+    A, B, Cm = synth.random_small(rng, 2, nk, 3, p=1.0, sizes=(32,), dist="wide", with_c=True, c_p=1.0)
+    got, _ = gpu_multiply("N", "N", -1.5, A, B, 0.25, Cm, path="stacks", precision="ozaki", kernel=kernel)
+    ref, _, _ = emul_ref("N", "N", A, B, Cm, -1.5, 0.25, 7)
+    assert_same_pattern(got, ref)
+    assert np.array_equal(got.data, ref.data)
+
+
+def test_auto_kernel_choice_matches_both():
+    # 32 x 32 blocks pick the tcgen05 kernel, mixed small blocks the mma.sync one;
+    # both agree bit for bit with each other
+    w = synth.workload_precision_sparse(seed=7, nblk=16, occ=0.2)
+    g0, _ = gpu_multiply("N", "N", 1.0, w.A, w.B, 0.0, path="stacks", precision="ozaki", kernel=0)
+    g1, _ = gpu_multiply("N", "N", 1.0, w.A, w.B, 0.0, path="stacks", precision="ozaki", kernel=1)
+    g2, _ = gpu_multiply("N", "N", 1.0, w.A, w.B, 0.0, path="stacks", precision="ozaki", kernel=2)
+    assert np.array_equal(g0.data, g1.data) and np.array_equal(g1.data, g2.data)
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_emulated_stacks_meet_1e12_and_integer_exact(kernel):
     w = synth.workload_precision_sparse(seed=6, nblk=20, occ=0.2)
-    got, _ = gpu_multiply("N", "N", 1.0, w.A, w.B, 0.0, path="stacks", precision="ozaki")
+    got, _ = gpu_multiply("N", "N", 1.0, w.A, w.B, 0.0, path="stacks", precision="ozaki", kernel=kernel)
     ref = O.multiply("N", "N", 1.0, w.A, w.B, 0.0)
     err = O.normwise_error(O.densify(got), O.densify(ref), O.densify(w.A), O.densify(w.B))
     assert err <= 1e-12
     rng = np.random.default_rng(610)
     A, B, _ = synth.random_small(rng, 6, 6, 6, p=0.5, sizes=(5, 13, 32), dist="int")
-    got, _ = gpu_multiply("N", "N", 1.0, A, B, 0.0, path="stacks", precision="ozaki", ozaki_slices=2)
+    got, _ = gpu_multiply("N", "N", 1.0, A, B, 0.0, path="stacks", precision="ozaki", ozaki_slices=2,
+                          kernel=kernel)
     assert np.array_equal(got.data, O.multiply("N", "N", 1.0, A, B, 0.0).data)
 
 
