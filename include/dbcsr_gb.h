@@ -72,6 +72,9 @@ typedef void (*dbcsr_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
 #define DBCSR_PATH_AUTO   0  /* dense path when op(A) and op(B) are 100% occupied, else stacks */
 #define DBCSR_PATH_STACKS 1  /* stacks of block products, batched small-GEMM kernels */
 #define DBCSR_PATH_DENSE  2  /* densify, one GEMM, undensify (any occupancy; absent blocks = 0) */
+#define DBCSR_PATH_HYBRID 3  /* per panel of block rows of op(A): densified GEMM where the panel
+                                (and op(B)) is at least hybrid_fill_pct % occupied, stacks elsewhere
+                                (Sec. III's densification applied to parts of a sparse matrix) */
 
 /* Arithmetic of the multiply. */
 #define DBCSR_PREC_FP64  0   /* IEEE FP64 products and sums (DFMA / DMMA) */
@@ -102,7 +105,9 @@ typedef struct {
                           (patterns unchanged, values may change), same op(),
                           alpha and beta, into the C it produced, skips stack
                           generation and replays the graph, updating C in place */
-    int reserved[2];   /* must be zero                                        */
+    int hybrid_panel;  /* DBCSR_PATH_HYBRID: block rows per panel; 0 = about 1024 element rows */
+    int hybrid_fill_pct; /* DBCSR_PATH_HYBRID: occupancy (percent of elements) from which a panel
+                            is densified; 0 = 50                                   */
 } dbcsr_opts;
 
 /* Statistics of the last dbcsr_multiply on the calling thread. */
@@ -115,7 +120,7 @@ typedef struct {
     int path;                /* path taken (DBCSR_PATH_STACKS or _DENSE)          */
     int precision;           /* precision used                                    */
     int kernel_launches;     /* kernels this library launched during the call     */
-    int reserved;
+    int dense_panels;        /* DBCSR_PATH_HYBRID: panels computed densely        */
     /* with dbcsr_opts.timing: milliseconds per phase, CUDA events on the stream */
     float ms_setup;          /* stack generation, or densification of A, B, C    */
     float ms_main;           /* the product kernels (batched small GEMM / GEMM)   */

@@ -14,6 +14,13 @@ kernel timer, keeps the fastest and writes the table as JSON:
 ``load_table`` hands a table to the library (dbcsr_set_tuning).
 
 Usage (on the GPU): python -m paper_1910_04796_gb300.autotune --sizes 5 13 23 26 32 --out table.json
+
+With --model the tuner times only a random fraction of the (m, n, k) shapes,
+fits the regression-tree performance model of ``perfmodel`` to them and
+predicts the variant of every (m, n) up to --max-edge (the paper's approach
+to a kernel space too large to time exhaustively); with --evaluate it also
+times the held-out shapes and reports how close the predicted choices come
+to the measured optimum.
 """
 from __future__ import annotations
 
@@ -58,6 +65,44 @@ def tune_shape(m, n, ksizes, reps=3, seed=0):
     return best, res
 
 
+def measure(shapes, reps=3, seed=0):
+    """Records (m, n, k, variant, TFLOP/s) of every variant on each (m, n, k) shape."""
+    out = []
+    for i, (m, n, k) in enumerate(shapes):
+        _, res = tune_shape(int(m), int(n), [int(k)], reps, seed + i)
+        out += [(int(m), int(n), int(k), v, float(t)) for v, t in res.items()]
+    return out
+
+
+def model_tune(sizes, train_frac, reps, max_edge, evaluate, seed=0):
+    """Fit the performance model on a random subset of shapes; returns (table entries, report)."""
+    import itertools
+    from . import perfmodel
+    shapes = list(itertools.product(sizes, sizes, sizes))
+    rng = np.random.default_rng(seed)
+    rng.shuffle(shapes)
+    ntrain = max(1, int(round(train_frac * len(shapes))))
+    train, held = shapes[:ntrain], shapes[ntrain:]
+    recs = measure(train, reps, seed)
+    model = perfmodel.PerfModel(perfmodel.RandomForest(seed=seed)).fit(recs)
+    edges = range(1, max_edge + 1)
+    entries = [[m, n, v, t, {}] for (m, n, v, t) in model.table(edges, edges, sizes)]
+    report = {"shapes": len(shapes), "timed_for_training": len(train), "train_frac": train_frac,
+              "sizes": list(map(int, sizes))}
+    if evaluate and held:
+        hrec = measure(held, reps, seed + 10_000)
+        measured = {}
+        for (m, n, k, v, t) in hrec:
+            measured.setdefault((m, n, k), {})[v] = t
+        chosen = {s: model.best_variant(*s) for s in measured}
+        report["held_out_model"] = perfmodel.choice_quality(measured, chosen)
+        report["held_out_default_variant0"] = perfmodel.choice_quality(measured, {s: 0 for s in measured})
+        # the table the library actually uses is per (m, n): score that choice too
+        tab = {(e[0], e[1]): e[2] for e in entries}
+        report["held_out_mn_table"] = perfmodel.choice_quality(measured, {s: tab[(s[0], s[1])] for s in measured})
+    return entries, report
+
+
 def tune(msizes, nsizes, ksizes, reps=3):
     entries = []
     for m in msizes:
@@ -82,9 +127,25 @@ def main():
     ap.add_argument("--sizes", type=int, nargs="+", default=[5, 13, 22, 23, 26, 32])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--out", default=DEFAULT_TABLE)
+    ap.add_argument("--model", action="store_true", help="time a subset, predict the rest (regression trees)")
+    ap.add_argument("--train-frac", type=float, default=0.2)
+    ap.add_argument("--max-edge", type=int, default=32, help="table covers m, n = 1 .. max-edge")
+    ap.add_argument("--evaluate", action="store_true", help="also time the held-out shapes and score the model")
+    ap.add_argument("--report", default=None, help="JSON file for the model's evaluation")
     args = ap.parse_args()
     import torch
     dbcsr.init()
+    if args.model:
+        entries, report = model_tune(args.sizes, args.train_frac, args.reps, args.max_edge, args.evaluate)
+        with open(args.out, "w") as f:
+            json.dump({"device": torch.cuda.get_device_name(), "kernel": "FP64 stack kernels",
+                       "model": "random forest of regression trees", "report": report, "entries": entries},
+                      f, indent=1)
+        if args.report:
+            with open(args.report, "w") as f:
+                json.dump(report, f, indent=1)
+        print(json.dumps(report, indent=1))
+        return
     entries = tune(args.sizes, args.sizes, args.sizes, args.reps)
     os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)
     with open(args.out, "w") as f:

@@ -565,9 +565,128 @@ bool plan_matches(const ReusePlan* rp, bool ta, bool tb, double alpha, double be
            rp->alpha == alpha && rp->beta == beta && rp->use_old == (beta != 0.0);
 }
 
+// The product kernels over C blocks [b0, b1) of the plan (one contiguous run
+// of C block rows): the same arguments with the C-block arrays offset.
+int stack_run(const SmmArgs& g0, int64_t b0, int64_t b1, int64_t nprod, dbcsr_matrix_s* A, bool ta,
+              dbcsr_matrix_s* B, bool tb, dbcsr_matrix_s* C, const dbcsr_opts& o, double* flops) {
+    if (b1 <= b0) return DBCSR_OK;
+    SmmArgs g = g0;
+    g.nC = b1 - b0;
+    g.c_row += b0;
+    g.c_col += b0;
+    g.c_off += b0;
+    if (g.c_old) g.c_old += b0;
+    g.c_pstart += b0;
+    DB_CUDA(cudaMemsetAsync(g.counter, 0, sizeof(unsigned long long), g_ctx.stream));
+    if (o.precision == DBCSR_PREC_FP64) return smm_fp64_dispatch(g, C->max_rs * C->max_cs, o.kernel);
+    double f = 0.0;
+    DB_TRY(smm_emulated(g, A, ta, B, tb, C, o, nprod, &f));
+    *flops += f;
+    return DBCSR_OK;
+}
+
+// Hybrid partial densification: Sec. III coalesces all blocks of a dense
+// operand into one block; here the decision is taken per panel of consecutive
+// block rows of op(A). A panel whose stored elements fill at least
+// hybrid_fill_pct % of it (with op(B) at least as full) is densified:
+// dense panel of op(A) x dense op(B) (+ beta x the dense panel of old C) in one
+// GEMM of the requested precision, then split into the plan's C blocks of
+// those rows; the other panels run the stack kernels on their C blocks. Every
+// C block is written by exactly one of the two.
+int hybrid_products(const SmmArgs& g, const StackPlan& P, double* data, bool ta, bool tb, double alpha,
+                    dbcsr_matrix_s* A, dbcsr_matrix_s* B, double beta, bool use_old, dbcsr_matrix_s* C,
+                    const dbcsr_opts& o) {
+    if (o.precision == DBCSR_PREC_TF32)
+        return fail(DBCSR_ERR_ARG, "hybrid path: TF32 has no stack kernels; use the dense path");
+    const int nrows = C->nbr;
+    const int64_t N = C->h_coff[C->nbc];
+    const int64_t K = ta ? A->h_roff[A->nbr] : A->h_coff[A->nbc];
+    const std::vector<int>& rsz = C->h_rs;
+    // stored elements of op(A) per block row
+    DB_TRY(download_index(A));
+    std::vector<double> rowel(nrows, 0.0);
+    for (int i = 0; i < A->nbr; i++)
+        for (int b = A->h_rowptr[i]; b < A->h_rowptr[i + 1]; b++) {
+            const int j = A->h_col[b];
+            rowel[ta ? j : i] += (double)A->h_rs[i] * A->h_cs[j];
+        }
+    const double fillB = (K > 0 && N > 0) ? (double)B->nelems / ((double)K * (double)N) : 0.0;
+    const double theta = (o.hybrid_fill_pct > 0 ? o.hybrid_fill_pct : 50) / 100.0;
+    int prow = o.hybrid_panel;
+    if (prow <= 0) {
+        const double avg = nrows > 0 ? (double)C->h_roff[nrows] / nrows : 1.0;
+        prow = std::max(1, (int)std::ceil(1024.0 / std::max(avg, 1.0)));
+    }
+    // runs of consecutive panels with the same decision
+    std::vector<std::pair<int, int>> runs;   // [r0, r1)
+    std::vector<char> dense_run;
+    for (int r0 = 0; r0 < nrows; r0 += prow) {
+        const int r1 = std::min(nrows, r0 + prow);
+        double el = 0.0, cap = 0.0;
+        for (int r = r0; r < r1; r++) {
+            el += rowel[r];
+            cap += (double)rsz[r] * (double)K;
+        }
+        const bool dense = K > 0 && cap > 0.0 && el / cap >= theta && fillB >= theta;
+        g_stats.dense_panels += dense ? 1 : 0;
+        if (!runs.empty() && (bool)dense_run.back() == dense && runs.back().second == r0)
+            runs.back().second = r1;
+        else {
+            runs.push_back({r0, r1});
+            dense_run.push_back(dense ? 1 : 0);
+        }
+    }
+    // C block ranges of block rows and product ranges of C blocks (host copies)
+    std::vector<int> crp(nrows + 1);
+    DB_TRY(d2h(crp.data(), P.c_rowptr, sizeof(int) * (nrows + 1)));
+    std::vector<int64_t> ps(P.nC + 1);
+    DB_TRY(d2h(ps.data(), P.c_pstart, sizeof(int64_t) * (P.nC + 1)));
+    DBuf<double> dB, dA, dC;
+    bool have_b = false;
+    double flops = 0.0, useful_dense = 0.0;   // useful_dense: products of the dense runs
+    for (size_t q = 0; q < runs.size(); q++) {
+        const int r0 = runs[q].first, r1 = runs[q].second;
+        const int64_t b0 = crp[r0], b1 = crp[r1];
+        if (!dense_run[q]) {
+            DB_TRY(stack_run(g, b0, b1, ps[b1] - ps[b0], A, ta, B, tb, C, o, &flops));
+            continue;
+        }
+        if (!have_b) {
+            DB_TRY(dB.alloc((size_t)std::max<int64_t>(K * N, 1)));
+            DB_TRY(densify(B, tb, dB.p, K, B->nblks != (int64_t)B->nbr * B->nbc));
+            have_b = true;
+        }
+        const int64_t Mr = C->h_roff[r1] - C->h_roff[r0];
+        DB_TRY(dA.alloc((size_t)std::max<int64_t>(Mr * K, 1)));
+        DB_TRY(dC.alloc((size_t)std::max<int64_t>(Mr * N, 1)));
+        DB_TRY(densify_rows(A, ta, r0, r1, dA.p, Mr));
+        if (use_old) DB_TRY(densify_rows(C, false, r0, r1, dC.p, Mr));
+        const double beta_eff = use_old ? beta : 0.0;
+        if (o.precision == DBCSR_PREC_FP64) {
+            DB_TRY(dgemm_fp64(Mr, N, K, alpha, dA.p, Mr, dB.p, K, beta_eff, dC.p, Mr));
+            flops += 2.0 * (double)Mr * (double)N * (double)K;
+        } else {
+            double f = 0.0;
+            DB_TRY(dgemm_emulated(Mr, N, K, alpha, dA.p, Mr, dB.p, K, beta_eff, dC.p, Mr, o, &f));
+            flops += f;
+        }
+        useful_dense += ps[b1] - ps[b0];
+        DB_TRY(undensify_blocks(b0, b1, P.c_row, P.c_col, P.c_off, data, C, dC.p, Mr, C->h_roff[r0]));
+    }
+    // main_flops: the dense GEMMs' arithmetic, plus for FP64 stack runs their
+    // products at the average useful flops per product (emulated runs report
+    // their own tensor-core arithmetic)
+    if (o.precision == DBCSR_PREC_FP64) {
+        const double avg = P.nprod > 0 ? g_stats.useful_flops / (double)P.nprod : 0.0;
+        flops += avg * ((double)P.nprod - useful_dense);
+    }
+    g_stats.main_flops = flops;
+    return DBCSR_OK;
+}
+
 int multiply_stacks(bool ta, bool tb, double alpha, dbcsr_matrix_s* A, dbcsr_matrix_s* B, double beta,
                     dbcsr_matrix_s* C, const dbcsr_opts& o) {
-    const bool reuse = o.reuse_plan != 0 && o.precision == DBCSR_PREC_FP64;
+    const bool reuse = o.reuse_plan != 0 && o.precision == DBCSR_PREC_FP64 && o.path != DBCSR_PATH_HYBRID;
     if (reuse && plan_matches(static_cast<ReusePlan*>(C->plan), ta, tb, alpha, beta, A, B, C)) {
         // same patterns into the C this plan produced: replay the product kernel in place
         ReusePlan* rp = static_cast<ReusePlan*>(C->plan);
@@ -617,7 +736,9 @@ int multiply_stacks(bool ta, bool tb, double alpha, dbcsr_matrix_s* A, dbcsr_mat
     g.counter = counter.p;
     int rc;
     mark(1);
-    if (o.precision == DBCSR_PREC_FP64) {
+    if (o.path == DBCSR_PATH_HYBRID) {
+        rc = hybrid_products(g, P, data, ta, tb, alpha, A, B, beta, use_old, C, o);
+    } else if (o.precision == DBCSR_PREC_FP64) {
         timer_kernel_begin();
         rc = smm_fp64_dispatch(g, C->max_rs * C->max_cs, o.kernel);
         timer_kernel_end();
@@ -811,7 +932,8 @@ extern "C" int dbcsr_multiply(char transa, char transb, double alpha, dbcsr_matr
         return fail(DBCSR_ERR_ARG, "multiply: trans must be 'N', 'T' or 'C'");
     dbcsr_opts o{};
     if (opts) o = *opts;
-    if (o.path < 0 || o.path > 2 || o.precision < 0 || o.precision > 2 || o.ozaki_slices < 0 || o.ozaki_slices > 12)
+    if (o.path < 0 || o.path > 3 || o.precision < 0 || o.precision > 2 || o.ozaki_slices < 0 ||
+        o.ozaki_slices > 12 || o.hybrid_panel < 0 || o.hybrid_fill_pct < 0 || o.hybrid_fill_pct > 100)
         return fail(DBCSR_ERR_ARG, "multiply: invalid options");
     DB_TRY(ensure_device());
     const bool ta = is_trans(transa), tb = is_trans(transb);
@@ -832,6 +954,7 @@ extern "C" int dbcsr_multiply(char transa, char transb, double alpha, dbcsr_matr
     PhaseTimer timer;
     timer.init(o.timing != 0);
     g_timer = timer.on ? &timer : nullptr;
+    // the hybrid path is the stack path with some panels of C block rows densified
     int rc = (path == DBCSR_PATH_DENSE) ? multiply_dense(ta, tb, alpha, A, B, beta, C, o)
                                         : multiply_stacks(ta, tb, alpha, A, B, beta, C, o);
     g_timer = nullptr;

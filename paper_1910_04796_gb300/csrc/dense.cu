@@ -31,13 +31,17 @@ __global__ void __launch_bounds__(256) k_densify(int64_t nblks, const int* __res
                                                  const int* __restrict__ rs, const int* __restrict__ cs,
                                                  const int64_t* __restrict__ roff,
                                                  const int64_t* __restrict__ coff, int trans,
-                                                 double* __restrict__ dense, int64_t ld) {
+                                                 double* __restrict__ dense, int64_t ld, int lo, int hi,
+                                                 int64_t base) {
+    // only blocks whose op() block row lies in [lo, hi); op() element rows shift by -base
     __shared__ double tile[32][33];
     for (int64_t b = blockIdx.x; b < nblks; b += gridDim.x) {
         const int i = row_of[b], j = col[b];
+        const int oprow = trans ? j : i;
+        if (oprow < lo || oprow >= hi) continue;
         const int m = rs[i], n = cs[j];
         const double* blk = data + off[b];
-        const int64_t r0 = roff[i], c0 = coff[j];
+        const int64_t r0 = roff[i] - (trans ? 0 : base), c0 = coff[j] - (trans ? base : 0);
         for (int tr = 0; tr < m; tr += 32)
             for (int tc = 0; tc < n; tc += 32) {
                 const int x = threadIdx.x & 31, y = threadIdx.x >> 5;   // 32 x 8
@@ -68,12 +72,13 @@ __global__ void __launch_bounds__(256) k_undensify(int64_t nblks, const int* __r
                                                    const int* __restrict__ rs, const int* __restrict__ cs,
                                                    const int64_t* __restrict__ roff,
                                                    const int64_t* __restrict__ coff,
-                                                   const double* __restrict__ dense, int64_t ld) {
+                                                   const double* __restrict__ dense, int64_t ld, int64_t base) {
+    // dense row of element row r: r - base
     for (int64_t b = blockIdx.x; b < nblks; b += gridDim.x) {
         const int i = row_of[b], j = col[b];
         const int m = rs[i], n = cs[j];
         double* blk = data + off[b];
-        const int64_t r0 = roff[i], c0 = coff[j];
+        const int64_t r0 = roff[i] - base, c0 = coff[j];
         const int mn = m * n;
         for (int e = threadIdx.x; e < mn; e += blockDim.x) {
             int r = e % m, c = e / m;
@@ -183,7 +188,32 @@ int densify(const dbcsr_matrix_s* m, bool trans, double* dense, int64_t ld, bool
     if (m->nblks == 0) return DBCSR_OK;
     int grid = (int)std::min<int64_t>(m->nblks, (int64_t)ctx().num_sms * 16);
     k_densify<<<grid, 256, 0, st>>>(m->nblks, m->d_row_of, m->d_col, m->d_off, m->d_data, m->d_rs, m->d_cs,
-                                    m->d_roff, m->d_coff, trans ? 1 : 0, dense, ld);
+                                    m->d_roff, m->d_coff, trans ? 1 : 0, dense, ld, 0, INT32_MAX, 0);
+    DB_KCHECK();
+    return DBCSR_OK;
+}
+
+int densify_rows(const dbcsr_matrix_s* m, bool trans, int lo, int hi, double* dense, int64_t ld) {
+    cudaStream_t st = ctx().stream;
+    const std::vector<int64_t>& ro = trans ? m->h_coff : m->h_roff;
+    const int64_t base = ro[lo], rows = ro[hi] - base;
+    const int64_t cols = trans ? m->h_roff[m->nbr] : m->h_coff[m->nbc];
+    if (rows * cols > 0) DB_CUDA(cudaMemsetAsync(dense, 0, sizeof(double) * (size_t)(ld * (cols - 1) + rows), st));
+    if (m->nblks == 0) return DBCSR_OK;
+    int grid = (int)std::min<int64_t>(m->nblks, (int64_t)ctx().num_sms * 16);
+    k_densify<<<grid, 256, 0, st>>>(m->nblks, m->d_row_of, m->d_col, m->d_off, m->d_data, m->d_rs, m->d_cs,
+                                    m->d_roff, m->d_coff, trans ? 1 : 0, dense, ld, lo, hi, base);
+    DB_KCHECK();
+    return DBCSR_OK;
+}
+
+int undensify_blocks(int64_t b0, int64_t b1, const int* row_of, const int* col, const int64_t* off, double* data,
+                     const dbcsr_matrix_s* shape, const double* dense, int64_t ld, int64_t base) {
+    if (b1 <= b0) return DBCSR_OK;
+    cudaStream_t st = ctx().stream;
+    int grid = (int)std::min<int64_t>(b1 - b0, (int64_t)ctx().num_sms * 16);
+    k_undensify<<<grid, 256, 0, st>>>(b1 - b0, row_of + b0, col + b0, off + b0, data, shape->d_rs, shape->d_cs,
+                                      shape->d_roff, shape->d_coff, dense, ld, base);
     DB_KCHECK();
     return DBCSR_OK;
 }
@@ -193,7 +223,7 @@ int undensify(dbcsr_matrix_s* m, const double* dense, int64_t ld) {
     cudaStream_t st = ctx().stream;
     int grid = (int)std::min<int64_t>(m->nblks, (int64_t)ctx().num_sms * 16);
     k_undensify<<<grid, 256, 0, st>>>(m->nblks, m->d_row_of, m->d_col, m->d_off, m->d_data, m->d_rs, m->d_cs,
-                                      m->d_roff, m->d_coff, dense, ld);
+                                      m->d_roff, m->d_coff, dense, ld, 0);
     DB_KCHECK();
     return DBCSR_OK;
 }

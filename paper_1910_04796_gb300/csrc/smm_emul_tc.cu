@@ -18,20 +18,27 @@
 // brings all s slices of a block into shared memory. Per product two MMA
 // groups, each K = 32 (two K = 16 instructions):
 //   G1: rows A slices 1..4 (M = 128) x columns B slices 1..s (N = 32 s)
-//   G2: rows A slices 5..8 (M = 128) x columns B slices 1..s-4 (N = 32 (s-4))
-// so pair (t, u) owns the 32 x 32 accumulator block at TMEM lanes 32 (t-1)
-// (mod 128) and columns 32 (u-1) (+ 32 s for G2); pairs with t + u > s + 1
+//   G2: rows A slices s, s-1, .., 5 (M = 128, padded) x columns B slices
+//       1..s-4 (N = 32 (s-4)); A's slices are stored in the order
+//       1, 2, 3, 4, s, s-1, .., 5 so that G2 is one operand and every lane
+//       quadrant q holds the slices q + 1 and s - q, which balances the
+//       epilogue's work over the quadrants
+// so pair (t, u) owns a 32 x 32 accumulator block of TMEM (lane quadrant
+// t - 1 or s - t, columns 32 (u-1), + 32 s for G2); pairs with t + u > s + 1
 // are computed and ignored. An fp32 accumulator is exact for 32 products
 // (32 * 32 * 127^2 < 2^24): a C block's products run in chunks of 32.
 //
 // Warps: 0 bulk-copy producer (one lane), 1 TMEM owner and MMA issuer (one
-// lane), 2-5 epilogue; epilogue warp w reads TMEM lane quadrant q = w % 4,
-// i.e. A slice t = q + 1 of G1 and t = q + 5 of G2. Per chunk the epilogue
+// lane), 2-9 epilogue; epilogue warp w reads TMEM lane quadrant q = w % 4,
+// i.e. A slice t = q + 1 of G1 and t = s - q of G2, two warps per quadrant
+// splitting the columns. Every role reads its C blocks from a schedule in
+// traversal order (product range, offsets, sizes in one record) and loads
+// the next record ahead. Per chunk the epilogue
 //   1. drains TMEM: level d's contribution of its slices, P_{t,d-t} (+ the
 //      G2 term), converted exactly to int32, into a level block in shared
 //      memory; then releases TMEM, so the next chunk's MMAs overlap the rest;
 //   2. sums the level blocks of the four quadrants into per-thread int32
-//      level sums (thread: row i = lane, columns 8 q .. 8 q + 7).
+//      level sums (thread: row i = lane, four columns).
 // After the C block's last chunk it recombines, rounds, scales and stores.
 // int32 level sums are exact while products * s * 32 * 127^2 < 2^31 (checked
 // on the host). Every wait is bounded (4 s): on expiry the kernel sets the
@@ -48,12 +55,19 @@ namespace dbcsr {
 
 namespace {
 
-constexpr int TC_THREADS = 192;
+constexpr int TC_R = 2;                       // epilogue warps per TMEM lane quadrant
+constexpr int TC_EPI = 4 * TC_R;              // epilogue warps
+constexpr int TC_THREADS = 64 + 32 * TC_EPI;  // producer warp, MMA warp, epilogue
+constexpr int TC_COLS = 32 / TC_R;            // accumulator columns an epilogue warp drains per block
+constexpr int TC_EL = 8 / TC_R;               // C elements per epilogue thread
 constexpr int TC_SLOT = 2048;                 // one 32 x 32 bf16 slice
 constexpr int TC_SMEM_CAP = 232448;           // 227 KB of shared memory per CTA
 constexpr int TC_SMEM_MIN = 120 * 1024;       // one CTA per SM: it allocates all 512 TMEM columns
 constexpr int TC_CHUNK = 32;                  // products per exact fp32 stretch
 constexpr uint64_t TC_WAIT_NS = 4000000000ull;
+// C blocks are visited tile by tile: the CTAs working at the same time share
+// the tile's A block rows and B block columns, which stay in L2
+constexpr int TC_TILE = 32;
 
 template <int S>
 struct TcGeo {
@@ -80,32 +94,35 @@ __host__ __device__ constexpr int lvl_blk(int w, int d) {
     return w * S - w * (w - 1) / 2 + (d - w - 2);
 }
 
+// One C block in traversal order: everything the three roles need, one record.
+struct __align__(16) TcBlk {
+    int64_t p0, p1;         // products [p0, p1)
+    int64_t c_off;          // element offset of the new C block
+    int64_t old_off;        // element offset of the old C block (beta != 0), -1: none
+    int64_t rbase, cbase;   // first element row / column of the block
+    int m, n;               // block sizes
+    int64_t pad;
+};
+static_assert(sizeof(TcBlk) == 64, "schedule record is four 16-byte loads");
+
 struct TcArgs {
     int64_t nC;
-    const int* c_row;
-    const int* c_col;
-    const int64_t* c_off;
-    const int* c_old;
-    const int64_t* c_pstart;
+    const TcBlk* sched;
     const int2* prod;
-    const int* rsC;
-    const int* csC;
-    const int64_t* croff;
-    const int64_t* ccoff;
     const int* e;               // exponents of C's element rows
     const int* f;               // exponents of C's element columns
     const uint8_t* SA;          // s slices (2 KB each) per stored A block
     const uint8_t* SB;
     double* Cd;
     const double* Cold;
-    const int64_t* Cold_off;
     double alpha, beta;
     int* err;
 };
 
 // Slices of every stored block in the operand layout above, zero-padded to
 // 32 x 32: warp per block, lane per 8-element chunk of a row.
-__global__ void k_tc_slice(SliceGeom G, const int* __restrict__ ex, int s, uint8_t* __restrict__ out) {
+// A (is_a) stores slice t in slot t - 1 for t <= 4 and 4 + s - t above; B in slot t - 1.
+__global__ void k_tc_slice(SliceGeom G, const int* __restrict__ ex, int s, int is_a, uint8_t* __restrict__ out) {
     const int lane = threadIdx.x & 31;
     const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -133,10 +150,50 @@ __global__ void k_tc_slice(SliceGeom G, const int* __restrict__ ex, int s, uint8
                                                                  emul::slice_bf16(q[2 * k + 1], t, s));
                     w[k] = *reinterpret_cast<const uint32_t*>(&pr);
                 }
-                *reinterpret_cast<uint4*>(o + (t - 1) * 1024 + pos) = make_uint4(w[0], w[1], w[2], w[3]);
+                const int slot = (is_a && t > 4) ? 4 + s - t : t - 1;
+                *reinterpret_cast<uint4*>(o + slot * 1024 + pos) = make_uint4(w[0], w[1], w[2], w[3]);
             }
         }
     }
+}
+
+// traversal key of each C block: its tile, row-major over tiles
+__global__ void k_tile_keys(int64_t nC, const int* __restrict__ c_row, const int* __restrict__ c_col,
+                            int tiles_c, uint32_t* __restrict__ key, uint32_t* __restrict__ idx) {
+    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= nC) return;
+    key[b] = (uint32_t)(c_row[b] / TC_TILE) * (uint32_t)tiles_c + (uint32_t)(c_col[b] / TC_TILE);
+    idx[b] = (uint32_t)b;
+}
+
+__global__ void k_tc_sched(int64_t nC, const uint32_t* __restrict__ order, const int* __restrict__ c_row,
+                           const int* __restrict__ c_col, const int64_t* __restrict__ c_pstart,
+                           const int64_t* __restrict__ c_off, const int* __restrict__ c_old,
+                           const int64_t* __restrict__ cold_off, const int* __restrict__ rsC,
+                           const int* __restrict__ csC, const int64_t* __restrict__ croff,
+                           const int64_t* __restrict__ ccoff, TcBlk* __restrict__ out) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= nC) return;
+    const int64_t cb = order[q];
+    const int br = c_row[cb], bc = c_col[cb];
+    TcBlk b;
+    b.p0 = c_pstart[cb];
+    b.p1 = c_pstart[cb + 1];
+    b.c_off = c_off[cb];
+    const int old = c_old ? c_old[cb] : -1;
+    b.old_off = old >= 0 ? cold_off[old] : -1;
+    b.rbase = croff[br];
+    b.cbase = ccoff[bc];
+    b.m = rsC[br];
+    b.n = csC[bc];
+    b.pad = 0;
+    out[q] = b;
+}
+
+// the product range of schedule entry q (a beyond-the-end q gives an empty range)
+__device__ __forceinline__ longlong2 sched_range(const TcArgs& a, int64_t q) {
+    if (q >= a.nC) return make_longlong2(0, 0);
+    return *reinterpret_cast<const longlong2*>(a.sched + q);
 }
 
 // all lanes of the warp agree: the wait succeeded and no role aborted
@@ -169,9 +226,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_smm_emul_tc(TcArgs a) {
             ptx::mbar_init(&empty[i], 1);
         }
         ptx::mbar_init(tfull, 1);
-        ptx::mbar_init(tempty, 128);
-        ptx::mbar_init(sfull, 128);
-        ptx::mbar_init(sfree, 128);
+        ptx::mbar_init(tempty, 32 * TC_EPI);
+        ptx::mbar_init(sfull, 32 * TC_EPI);
+        ptx::mbar_init(sfree, 32 * TC_EPI);
         ptx::mbar_init(drain, 1);
         *abort_flag = 0;
         ptx::fence_mbar_init();
@@ -194,17 +251,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_smm_emul_tc(TcArgs a) {
             // ------------------------------------------------ bulk-copy producer
             int64_t it = 0;
             bool ok = true;
-            for (int64_t cb = blockIdx.x; cb < a.nC && ok; cb += gridDim.x) {
-                const int64_t p1 = a.c_pstart[cb + 1];
-                for (int64_t p = a.c_pstart[cb]; p < p1; p++, it++) {
+            longlong2 nxt = sched_range(a, blockIdx.x);
+            for (int64_t seq = blockIdx.x; seq < a.nC && ok; seq += gridDim.x) {
+                const longlong2 cur = nxt;
+                nxt = sched_range(a, seq + gridDim.x);
+                for (int64_t p = cur.x; p < cur.y; p++, it++) {
                     const int st = (int)(it % G::NST);
                     const uint32_t ph = (uint32_t)((it / G::NST) & 1);
+                    const int2 pr = a.prod[p];
                     if (*abort_flag || !ptx::mbar_wait_bounded(&empty[st], ph ^ 1u, TC_WAIT_NS)) {
                         if (!*abort_flag) on_timeout();
                         ok = false;
                         break;
                     }
-                    const int2 pr = a.prod[p];
                     uint8_t* sa = stages + st * G::STAGE;
                     ptx::mbar_arrive_expect_tx(&full[st], G::STAGE);
                     ptx::bulk_load(sa, a.SA + (int64_t)pr.x * (S * TC_SLOT), S * TC_SLOT, &full[st]);
@@ -224,16 +283,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_smm_emul_tc(TcArgs a) {
             // ------------------------------------------------------ MMA issuer
             int64_t it = 0, ci = 0;
             bool ok = true;
-            for (int64_t cb = blockIdx.x; cb < a.nC && ok; cb += gridDim.x) {
-                const int64_t p0 = a.c_pstart[cb], p1 = a.c_pstart[cb + 1];
-                for (int64_t c0 = p0; c0 < p1 && ok; c0 += TC_CHUNK, ci++) {
+            longlong2 nxt = sched_range(a, blockIdx.x);
+            for (int64_t seq = blockIdx.x; seq < a.nC && ok; seq += gridDim.x) {
+                const longlong2 cur = nxt;
+                nxt = sched_range(a, seq + gridDim.x);
+                for (int64_t c0 = cur.x; c0 < cur.y && ok; c0 += TC_CHUNK, ci++) {
                     if (*abort_flag || !ptx::mbar_wait_bounded(tempty, (uint32_t)((ci & 1) ^ 1), TC_WAIT_NS)) {
                         if (!*abort_flag) on_timeout();
                         ok = false;
                         break;
                     }
                     ptx::tc_fence_after();
-                    const int64_t c1 = c0 + TC_CHUNK < p1 ? c0 + TC_CHUNK : p1;
+                    const int64_t c1 = c0 + TC_CHUNK < cur.y ? c0 + TC_CHUNK : cur.y;
                     for (int64_t p = c0; p < c1; p++, it++) {
                         const int st = (int)(it % G::NST);
                         const uint32_t ph = (uint32_t)((it / G::NST) & 1);
@@ -266,19 +327,39 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_smm_emul_tc(TcArgs a) {
         }
     } else {
         // ---------------------------------------------------------- epilogue
-        const int q = warp & 3;
-        const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
-        const int t1 = q + 1, t2 = q + 5;
+        // warp (q, r): TMEM lane quadrant q = warp % 4, columns 16 r .. 16 r + 15
+        // of every 32-column accumulator block; in the sum and the final
+        // stage thread (warp (q, r), lane) owns row i = lane, columns 4 ep .. 4 ep + 3
+        const int q = warp & 3, r = (warp - 2) >> 2, ep = q * TC_R + r;
+        const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(r * TC_COLS);
+        const int t1 = q + 1, t2 = S - q;                 // A slices of quadrant q in G1 and G2
+        const bool has2 = (G::N2 > 0) && (t2 >= 5);
+        const int sw = lane & 7;   // 16-byte chunks XOR-swizzled by row: conflict-free stores and loads
+        const int i = lane;
         int64_t ci = 0;
         bool ok = true;
-        for (int64_t cb = blockIdx.x; cb < a.nC && ok; cb += gridDim.x) {
-            const int64_t p0 = a.c_pstart[cb], p1 = a.c_pstart[cb + 1];
-            int lv[S][8];
+        TcBlk nxt;
+        if (blockIdx.x < a.nC) nxt = a.sched[blockIdx.x];
+        for (int64_t seq = blockIdx.x; seq < a.nC && ok; seq += gridDim.x) {
+            const TcBlk cur = nxt;
+            if (seq + gridDim.x < a.nC) nxt = a.sched[seq + gridDim.x];
+            // what the final stage needs, loaded now: its latency hides behind the MMAs
+            const bool row_ok = i < cur.m;
+            const int ei = row_ok ? a.e[cur.rbase + i] : 0;
+            int fj[TC_EL];
+            double oldv[TC_EL];
+#pragma unroll
+            for (int k = 0; k < TC_EL; k++) {
+                const int j = TC_EL * ep + k;
+                fj[k] = j < cur.n ? a.f[cur.cbase + j] : 0;
+                oldv[k] = (row_ok && j < cur.n && cur.old_off >= 0) ? a.Cold[cur.old_off + (int64_t)j * cur.m + i] : 0.0;
+            }
+            int lv[S][TC_EL];
 #pragma unroll
             for (int d = 0; d < S; d++)
 #pragma unroll
-                for (int k = 0; k < 8; k++) lv[d][k] = 0;
-            for (int64_t c0 = p0; c0 < p1; c0 += TC_CHUNK, ci++) {
+                for (int k = 0; k < TC_EL; k++) lv[d][k] = 0;
+            for (int64_t c0 = cur.p0; c0 < cur.p1; c0 += TC_CHUNK, ci++) {
                 const uint32_t ph = (uint32_t)(ci & 1);
                 if (!warp_wait(tfull, ph, abort_flag) || !warp_wait(sfree, ph ^ 1u, abort_flag)) {
                     if (!*abort_flag) on_timeout();
@@ -286,25 +367,35 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_smm_emul_tc(TcArgs a) {
                     break;
                 }
                 ptx::tc_fence_after();
-                // 1. drain: level d of slice t1 (and t2), exact fp32 integers -> int32
+                // 1. drain, two levels per TMEM round trip: level d of slice t1
+                //    (G1, u = d - t1) plus slice t2 (G2, u = d - t2) where it exists;
+                //    exact fp32 integers -> int32 level blocks
                 if (t1 <= S) {
-                    for (int d = t1 + 1; d <= S + 1; d++) {
-                        const bool two = (G::N2 > 0) && (t2 <= S) && (d - t2 >= 1);
-                        uint32_t r1[32], r2[32];
-                        ptx::tmem_ld_32x32b_x32(tl + (uint32_t)((d - t1 - 1) * 32), r1);
-                        if (two) ptx::tmem_ld_32x32b_x32(tl + (uint32_t)(G::N1 + (d - t2 - 1) * 32), r2);
+                    for (int d0 = t1 + 1; d0 <= S + 1; d0 += 2) {
+                        const int d1 = d0 + 1;
+                        const bool h1 = d1 <= S + 1;
+                        const bool g0 = has2 && d0 - t2 >= 1, g1 = has2 && h1 && d1 - t2 >= 1;
+                        uint32_t ra[TC_COLS], rb[TC_COLS], rc[TC_COLS], rd[TC_COLS];
+                        ptx::tmem_ld_32x32b_x16(tl + (uint32_t)((d0 - t1 - 1) * 32), ra);
+                        if (h1) ptx::tmem_ld_32x32b_x16(tl + (uint32_t)((d1 - t1 - 1) * 32), rb);
+                        if (g0) ptx::tmem_ld_32x32b_x16(tl + (uint32_t)(G::N1 + (d0 - t2 - 1) * 32), rc);
+                        if (g1) ptx::tmem_ld_32x32b_x16(tl + (uint32_t)(G::N1 + (d1 - t2 - 1) * 32), rd);
                         ptx::tmem_wait_ld();
-                        uint8_t* row = stg + lvl_blk<S>(q, d) * 4096 + lane * 128;
+                        uint8_t* row0 = stg + lvl_blk<S>(q, d0) * 4096 + lane * 128;
+                        uint8_t* row1 = stg + lvl_blk<S>(q, h1 ? d1 : d0) * 4096 + lane * 128;
 #pragma unroll
-                        for (int c8 = 0; c8 < 8; c8++) {
-                            int v[4];
+                        for (int c = 0; c < TC_COLS / 4; c++) {
+                            int v0[4], v1[4];
 #pragma unroll
                             for (int k = 0; k < 4; k++) {
-                                v[k] = __float2int_rn(__uint_as_float(r1[c8 * 4 + k]));
-                                if (two) v[k] += __float2int_rn(__uint_as_float(r2[c8 * 4 + k]));
+                                v0[k] = __float2int_rn(__uint_as_float(ra[c * 4 + k]));
+                                if (g0) v0[k] += __float2int_rn(__uint_as_float(rc[c * 4 + k]));
+                                v1[k] = __float2int_rn(__uint_as_float(rb[c * 4 + k]));
+                                if (g1) v1[k] += __float2int_rn(__uint_as_float(rd[c * 4 + k]));
                             }
-                            // 16-byte chunks XOR-swizzled by row: conflict-free stores and loads
-                            *reinterpret_cast<int4*>(row + ((c8 ^ (lane & 7)) << 4)) = make_int4(v[0], v[1], v[2], v[3]);
+                            const int off = ((r * (TC_COLS / 4) + c) ^ sw) << 4;
+                            *reinterpret_cast<int4*>(row0 + off) = make_int4(v0[0], v0[1], v0[2], v0[3]);
+                            if (h1) *reinterpret_cast<int4*>(row1 + off) = make_int4(v1[0], v1[1], v1[2], v1[3]);
                         }
                     }
                 }
@@ -316,49 +407,42 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_smm_emul_tc(TcArgs a) {
                     ok = false;
                     break;
                 }
-                // 2. level sums of row i = lane, columns 8 q .. 8 q + 7
+                // 2. level sums of this thread's four elements
 #pragma unroll
                 for (int d = 2; d <= S + 1; d++)
 #pragma unroll
                     for (int w = 0; w < G::T1; w++)
                         if (w + 2 <= d) {
-                            const uint8_t* row = stg + lvl_blk<S>(w, d) * 4096 + lane * 128;
-                            const int4 x0 = *reinterpret_cast<const int4*>(row + (((2 * q) ^ (lane & 7)) << 4));
-                            const int4 x1 = *reinterpret_cast<const int4*>(row + (((2 * q + 1) ^ (lane & 7)) << 4));
-                            lv[d - 2][0] += x0.x;
-                            lv[d - 2][1] += x0.y;
-                            lv[d - 2][2] += x0.z;
-                            lv[d - 2][3] += x0.w;
-                            lv[d - 2][4] += x1.x;
-                            lv[d - 2][5] += x1.y;
-                            lv[d - 2][6] += x1.z;
-                            lv[d - 2][7] += x1.w;
+                            const int4 x = *reinterpret_cast<const int4*>(stg + lvl_blk<S>(w, d) * 4096 + lane * 128 +
+                                                                          ((ep ^ sw) << 4));
+                            lv[d - 2][0] += x.x;
+                            lv[d - 2][1] += x.y;
+                            lv[d - 2][2] += x.z;
+                            lv[d - 2][3] += x.w;
                         }
                 ptx::mbar_arrive(sfree);
             }
             if (!ok) break;
-            // 3. exact recombination, one rounding, alpha / beta, column-major C block
-            const int br = a.c_row[cb], bc = a.c_col[cb];
-            const int m = a.rsC[br], n = a.csC[bc];
-            const int i = lane;
-            if (i < m) {
-                const int64_t cbase = a.ccoff[bc];
-                const int ei = a.e[a.croff[br] + i];
-                double* cout = a.Cd + a.c_off[cb];
-                const int old = a.c_old ? a.c_old[cb] : -1;
-                const double* cold = old >= 0 ? a.Cold + a.Cold_off[old] : nullptr;
+            // 3. exact recombination, one rounding, alpha / beta, column-major C block.
+            // sum_d G_d 2^(7(s-1-d)) (d from 0) = U 2^(7 (s - NU)) + V with U over the
+            // first NU = min(4, s) levels and V over the rest: |U|, |V| < 2^53, so
+            // both run in int64 and one 128-bit shift and add joins them.
+            constexpr int NU = S < 4 ? S : 4;
+            if (row_ok) {
+                double* cout = a.Cd + cur.c_off;
 #pragma unroll
-                for (int k = 0; k < 8; k++) {
-                    const int j = 8 * q + k;
-                    if (j < n) {
-                        __int128 Sx = 0;
+                for (int k = 0; k < TC_EL; k++) {
+                    const int j = TC_EL * ep + k;
+                    if (j < cur.n) {
+                        long long U = 0, V = 0;
 #pragma unroll
-                        for (int d = 0; d < S; d++) Sx += (__int128)lv[d][k] << (7 * (S - 1 - d));
-                        double v = __dmul_rn(a.alpha,
-                                             emul::round_i128_scaled(Sx, ei + a.f[cbase + j] - 7 * (S + 1)));
-                        const int64_t idx = (int64_t)j * m + i;
-                        if (cold) v = __dadd_rn(v, __dmul_rn(a.beta, cold[idx]));
-                        cout[idx] = v;
+                        for (int d = 0; d < NU; d++) U = U * 128 + lv[d][k];
+#pragma unroll
+                        for (int d = NU; d < S; d++) V = V * 128 + lv[d][k];
+                        const __int128 Sx = (__int128)U * ((__int128)1 << (7 * (S - NU))) + V;
+                        double v = __dmul_rn(a.alpha, emul::round_i128_scaled(Sx, ei + fj[k] - 7 * (S + 1)));
+                        if (cur.old_off >= 0) v = __dadd_rn(v, __dmul_rn(a.beta, oldv[k]));
+                        cout[(int64_t)j * cur.m + i] = v;
                     }
                 }
             }
@@ -404,32 +488,40 @@ int smm_emul_tc(const SmmArgs& g, dbcsr_matrix_s* A, bool ta, dbcsr_matrix_s* B,
     DB_TRY(SB.alloc((size_t)(B->nblks ? B->nblks : 1) * s * TC_SLOT));
     const int sgrid = ctx().num_sms * 16;
     if (A->nblks > 0) {
-        k_tc_slice<<<(int)std::min<int64_t>(cdiv(A->nblks, 8), sgrid), 256, 0, st>>>(slice_geom(A, !ta), e, s, SA.p);
+        k_tc_slice<<<(int)std::min<int64_t>(cdiv(A->nblks, 8), sgrid), 256, 0, st>>>(slice_geom(A, !ta), e, s, 1, SA.p);
         DB_KCHECK();
     }
     if (B->nblks > 0) {
-        k_tc_slice<<<(int)std::min<int64_t>(cdiv(B->nblks, 8), sgrid), 256, 0, st>>>(slice_geom(B, tb), f, s, SB.p);
+        k_tc_slice<<<(int)std::min<int64_t>(cdiv(B->nblks, 8), sgrid), 256, 0, st>>>(slice_geom(B, tb), f, s, 0, SB.p);
         DB_KCHECK();
     }
+    // tile order (stable: row-major within a tile, as the C blocks are stored)
+    if (g.nC >= (int64_t)UINT32_MAX) return fail(DBCSR_ERR_OVERFLOW, "emulated stack kernel: too many C blocks");
+    DBuf<uint32_t> key, order;
+    DB_TRY(key.alloc(g.nC));
+    DB_TRY(order.alloc(g.nC));
+    const int tiles_r = (int)cdiv(C->nbr, TC_TILE), tiles_c = (int)cdiv(C->nbc, TC_TILE);
+    k_tile_keys<<<(unsigned)cdiv(g.nC, 256), 256, 0, st>>>(g.nC, g.c_row, g.c_col, tiles_c, key.p, order.p);
+    DB_KCHECK();
+    int bits = 0;
+    while (bits < 32 && ((uint64_t)1 << bits) < (uint64_t)tiles_r * tiles_c) bits++;
+    DB_TRY(radix_sort_u32(key.p, order.p, g.nC, bits));
+    DBuf<TcBlk> sched;
+    DB_TRY(sched.alloc(g.nC));
+    k_tc_sched<<<(unsigned)cdiv(g.nC, 256), 256, 0, st>>>(g.nC, order.p, g.c_row, g.c_col, g.c_pstart, g.c_off,
+                                                          g.c_old, g.Cold_off, g.rsC, g.csC, C->d_roff, C->d_coff,
+                                                          sched.p);
+    DB_KCHECK();
     TcArgs a;
     a.nC = g.nC;
-    a.c_row = g.c_row;
-    a.c_col = g.c_col;
-    a.c_off = g.c_off;
-    a.c_old = g.c_old;
-    a.c_pstart = g.c_pstart;
+    a.sched = sched.p;
     a.prod = g.prod;
-    a.rsC = g.rsC;
-    a.csC = g.csC;
-    a.croff = C->d_roff;
-    a.ccoff = C->d_coff;
     a.e = e;
     a.f = f;
     a.SA = SA.p;
     a.SB = SB.p;
     a.Cd = g.Cd;
     a.Cold = g.Cold;
-    a.Cold_off = g.Cold_off;
     a.alpha = g.alpha;
     a.beta = g.beta;
     a.err = ctx().d_flags;

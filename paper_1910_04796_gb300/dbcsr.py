@@ -16,10 +16,10 @@ from . import build as _build
 
 OK = 0
 ERR_ARG, ERR_DIM, ERR_ALLOC, ERR_OVERFLOW, ERR_TIMEOUT, ERR_CUDA, ERR_STATE = -1, -2, -3, -4, -5, -6, -7
-PATH_AUTO, PATH_STACKS, PATH_DENSE = 0, 1, 2
+PATH_AUTO, PATH_STACKS, PATH_DENSE, PATH_HYBRID = 0, 1, 2, 3
 PREC_FP64, PREC_OZAKI, PREC_TF32 = 0, 1, 2
 _PREC = {"fp64": PREC_FP64, "ozaki": PREC_OZAKI, "tf32": PREC_TF32}
-_PATH = {"auto": PATH_AUTO, "stacks": PATH_STACKS, "dense": PATH_DENSE}
+_PATH = {"auto": PATH_AUTO, "stacks": PATH_STACKS, "dense": PATH_DENSE, "hybrid": PATH_HYBRID}
 
 
 class DbcsrError(RuntimeError):
@@ -30,13 +30,14 @@ class DbcsrError(RuntimeError):
 
 class Opts(C.Structure):
     _fields_ = [("path", C.c_int), ("precision", C.c_int), ("ozaki_slices", C.c_int),
-                ("kernel", C.c_int), ("timing", C.c_int), ("reuse_plan", C.c_int), ("reserved", C.c_int * 2)]
+                ("kernel", C.c_int), ("timing", C.c_int), ("reuse_plan", C.c_int), ("hybrid_panel", C.c_int),
+                ("hybrid_fill_pct", C.c_int)]
 
 
 class Stats(C.Structure):
     _fields_ = [("n_products", C.c_int64), ("n_stacks", C.c_int64), ("n_shapes", C.c_int64),
                 ("c_blocks", C.c_int64), ("useful_flops", C.c_double), ("path", C.c_int),
-                ("precision", C.c_int), ("kernel_launches", C.c_int), ("reserved", C.c_int),
+                ("precision", C.c_int), ("kernel_launches", C.c_int), ("dense_panels", C.c_int),
                 ("ms_setup", C.c_float), ("ms_main", C.c_float), ("ms_finish", C.c_float),
                 ("ms_total", C.c_float), ("main_flops", C.c_double), ("main_bytes", C.c_double),
                 ("ms_kernel", C.c_float), ("reserved_f", C.c_float)]
@@ -241,8 +242,11 @@ class Matrix:
         return out.reshape((m, n), order="F") if found.value else None
 
 
-def opts(path="auto", precision="fp64", ozaki_slices=0, kernel=0, timing=False, reuse_plan=False) -> Opts:
+def opts(path="auto", precision="fp64", ozaki_slices=0, kernel=0, timing=False, reuse_plan=False,
+         hybrid_panel=0, hybrid_fill_pct=0) -> Opts:
     o = Opts()
+    o.hybrid_panel = int(hybrid_panel)
+    o.hybrid_fill_pct = int(hybrid_fill_pct)
     o.timing = 1 if timing else 0
     o.reuse_plan = 1 if reuse_plan else 0
     o.path = _PATH[path] if isinstance(path, str) else int(path)
@@ -253,9 +257,9 @@ def opts(path="auto", precision="fp64", ozaki_slices=0, kernel=0, timing=False, 
 
 
 def multiply(transa, transb, alpha, A: Matrix, B: Matrix, beta, Cm: Matrix, path="auto", precision="fp64",
-             ozaki_slices=0, kernel=0, timing=False, reuse_plan=False):
+             ozaki_slices=0, kernel=0, timing=False, reuse_plan=False, hybrid_panel=0, hybrid_fill_pct=0):
     """C = alpha*op(A)*op(B) + beta*C on the GPU (see dbcsr_multiply)."""
-    o = opts(path, precision, ozaki_slices, kernel, timing, reuse_plan)
+    o = opts(path, precision, ozaki_slices, kernel, timing, reuse_plan, hybrid_panel, hybrid_fill_pct)
     _check(load().dbcsr_multiply(transa.encode(), transb.encode(), float(alpha), A.handle, B.handle,
                                  float(beta), Cm.handle, C.byref(o)))
 

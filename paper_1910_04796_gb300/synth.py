@@ -209,6 +209,27 @@ def workload_precision_sparse(seed=5, nblk=1024, bs=32, occ=0.1):
     return Workload(f"precision-sparse-{nblk}x{nblk}-bs{bs}", A, B, None, 1.0, 0.0)
 
 
+def panel_mask(rng, nbr, nbc, panel, dense_every=2, sparse_occ=0.05):
+    """Block rows in panels of `panel` rows: every `dense_every`-th panel fully
+    occupied, the others Bernoulli(sparse_occ) -- a sparse matrix with dense
+    sub-panels (input of the hybrid path)."""
+    mask = rng.random((nbr, nbc)) < sparse_occ
+    for r0 in range(0, nbr, panel * dense_every):
+        mask[r0:r0 + panel, :] = True
+    return mask
+
+
+def workload_hybrid(seed=6, nblk=256, bs=32, panel=16, dense_every=2, sparse_occ=0.05, b_occ=1.0):
+    """nblk^2 grid of bs x bs blocks; A alternates dense and sparse panels of
+    `panel` block rows, B at b_occ occupancy (dense by default), U[-1,1], beta=0."""
+    rng = np.random.default_rng(seed)
+    rs = np.full(nblk, bs, np.int32)
+    A = make_matrix(rng, rs, rs, panel_mask(rng, nblk, nblk, panel, dense_every, sparse_occ))
+    B = make_matrix(rng, rs, rs, bernoulli_mask(rng, nblk, nblk, b_occ))
+    return Workload(f"hybrid-{nblk}x{nblk}-bs{bs}-panel{panel}", A, B, None, 1.0, 0.0,
+                    extra={"panel": panel, "sparse_occ": sparse_occ, "b_occ": b_occ})
+
+
 def random_small(rng, nbr, nbk, nbc, p=0.5, sizes=(1, 2, 3, 4, 5), dist="uniform",
                  with_c=False, c_p=0.3):
     """Tiny random block-sparse A (nbr x nbk), B (nbk x nbc) and optional C."""
