@@ -150,6 +150,10 @@ static int rows_build(const ob_mat *M, char op, ob_rows *v)
  * Every element sum runs over k ascending and, inside a block product, over
  * the inner index l ascending: acc += a[r,l]*b[l,c], then
  * C = (alpha*acc) + (beta*Cold). mode 1 carries the sum in double-double.
+ * mode 2 is the single-precision product the paper's library also accepts
+ * (Sec. II): each input element rounded to FP32 (nearest, ties to even), each
+ * product and each addition rounded to FP32, the same order; alpha and beta
+ * applied in FP64 to the FP32 sum.
  *
  * Rows: rows_sel (ascending, distinct) restricts the computation to those
  * block rows of C (NULL = all rows). Output in row order, columns ascending.
@@ -290,6 +294,15 @@ int oracle_multiply(char ta, char tb, double alpha, const ob_mat *A, const ob_ma
                                 }
                                 x[r + (int64_t)cc * m] = sh;
                                 cmp[j][r + (int64_t)cc * m] = sl;
+                            } else if (mode == 2) {
+                                float sum = (float)x[r + (int64_t)cc * m];   /* holds an FP32 value */
+                                for (int l = 0; l < kk; l++) {
+                                    float pa = (float)ablk[r + (int64_t)l * m];
+                                    float pb = (float)bblk[l + (int64_t)cc * kk];
+                                    float pr = pa * pb;
+                                    sum = sum + pr;
+                                }
+                                x[r + (int64_t)cc * m] = (double)sum;
                             } else {
                                 double sum = x[r + (int64_t)cc * m];
                                 for (int l = 0; l < kk; l++)

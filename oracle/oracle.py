@@ -109,7 +109,8 @@ def multiply(transa, transb, alpha, A, B, beta, Cm=None, rows=None, mode=0, nthr
     """C = alpha*op(A)*op(B) + beta*C (Sec. II). ``rows``: C block rows to compute.
 
     ``mode`` 0 = plain FP64 (k ascending, inner index ascending, no FMA
-    contraction); 1 = double-double accumulation (Dot2).
+    contraction); 1 = double-double accumulation (Dot2); 2 = FP32 (inputs
+    rounded to FP32, products and sums in FP32, alpha/beta in FP64).
     """
     keep = []
     a = _mk(A, keep)
