@@ -48,7 +48,7 @@ def peaks():
         return dict(FALLBACK), "fallback"
 
 
-def workload(name, scale):
+def workload(name, scale, occ=0.1):
     from paper_1910_04796_gb300 import synth
     if name == "dense-limit":
         nblk = max(2, int(round(512 * scale)))
@@ -64,6 +64,14 @@ def workload(name, scale):
     if name == "precision-sparse":
         nblk = max(8, int(round(1024 * scale)))
         return synth.workload_precision_sparse(seed=5, nblk=nblk)
+    if name == "hybrid":
+        nblk = max(16, int(round(256 * scale)))
+        return synth.workload_hybrid(seed=6, nblk=nblk, panel=max(1, nblk // 16))
+    if name == "occupancy":
+        nblk = max(8, int(round(256 * scale)))
+        w = synth.workload_precision_sparse(seed=7, nblk=nblk, occ=occ)
+        w.name = f"occupancy-{occ:g}-{nblk}x{nblk}-bs32"
+        return w
     if name.startswith("tall-skinny"):
         v = name.split("-")[-1]
         mn = max(64, int(round(4096 * scale / 32)) * 32)
@@ -191,7 +199,7 @@ def run_reference(args, world, rank):
     if rank != 0:
         return 0
     from oracle import oracle as O
-    w = workload(args.workload, args.scale)
+    w = workload(args.workload, args.scale, args.occ)
     nrows = len(w.A.col_sizes if w.transa in "TC" else w.A.row_sizes)
     threads = O.threads()
     rows = list(range(0, nrows, max(1, nrows // max(1, args.ref_rows))))[:args.ref_rows]
@@ -247,9 +255,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="dense-limit")
     ap.add_argument("--scale", type=float, default=1.0)
-    ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "ozaki", "tf32"])
-    ap.add_argument("--path", default="auto", choices=["auto", "stacks", "dense"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "ozaki", "tf32", "fp32"])
+    ap.add_argument("--path", default="auto", choices=["auto", "stacks", "dense", "hybrid"])
     ap.add_argument("--slices", type=int, default=0)
+    ap.add_argument("--occ", type=float, default=0.1, help="block occupancy of the 'occupancy' workload")
     ap.add_argument("--kernel", type=int, default=0,
                     help="stack kernel choice passed to dbcsr_multiply (0 = automatic)")
     ap.add_argument("--ref-rows", type=int, default=48, help="C block rows per oracle sample")
@@ -269,7 +278,7 @@ def main():
     pk, pk_kind = peaks()
     from paper_1910_04796_gb300 import autotune
     tuned = autotune.load_table()   # per-shape FP64 stack-kernel choice, if tuned on this GPU type
-    w = workload(args.workload, args.scale)
+    w = workload(args.workload, args.scale, args.occ)
     precision = args.precision
     if precision == "auto":
         precision = "ozaki" if dbcsr.has_precision("ozaki") else "fp64"
@@ -302,13 +311,14 @@ def main():
     for _ in range(max(1, min(3, args.steps))):
         step(timing=True)
         s2 = dbcsr.stats()
-        mains.append(s2["ms_kernel"])
+        # the hybrid path runs several product kernels: time the whole product phase
+        mains.append(s2["ms_main"] if s2["path"] == dbcsr.PATH_HYBRID else s2["ms_kernel"])
         totals.append(s2["ms_total"])
     main_ms = statistics.median(mains)
     s2 = dbcsr.stats()
-    path_taken = {dbcsr.PATH_DENSE: "dense", dbcsr.PATH_STACKS: "stacks"}[s2["path"]]
+    path_taken = {dbcsr.PATH_DENSE: "dense", dbcsr.PATH_STACKS: "stacks", dbcsr.PATH_HYBRID: "hybrid"}[s2["path"]]
     if precision == "fp64":
-        bound, unit = "tensor" if path_taken == "dense" else "alu", "TFLOP/s"
+        bound, unit = "alu" if path_taken == "stacks" else "tensor", "TFLOP/s"
         peak = pk["bf16_tflops"] * NOMINAL["fp64"] / NOMINAL["bf16"]
         peak_note = f"FP64 = {pk_kind} bf16 burst x nominal FP64/bf16 (1.25/2250)"
         achieved = s2["main_flops"] / (main_ms / 1e3) / 1e12
@@ -316,6 +326,14 @@ def main():
         bound, unit = "tensor", "TFLOP/s"
         peak = pk["bf16_tflops_sustained"] if main_ms > 1000 else pk["bf16_tflops"]
         peak_note = f"bf16 {'sustained' if main_ms > 1000 else 'burst'} ({pk_kind})"
+        achieved = s2["main_flops"] / (main_ms / 1e3) / 1e12
+    elif precision == "fp32":
+        # plain FP32 FMA on the CUDA cores: SMs x 128 lanes x 2 flops x the SM clock seen under load
+        bound, unit = "alu", "TFLOP/s"
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        mhz = clk.summary().get("sm_mhz") or clk.summary().get("sm_max_mhz") or 2070.0
+        peak = sms * 128 * 2 * mhz * 1e6 / 1e12
+        peak_note = f"FP32 FMA = {sms} SMs x 128 lanes x 2 x {mhz:.0f} MHz"
         achieved = s2["main_flops"] / (main_ms / 1e3) / 1e12
     else:
         bound, unit = "tensor", "TFLOP/s"
@@ -409,11 +427,13 @@ def main():
             "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
             "ms_per_step": 1000.0 * secs / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if precision == "fp64" else
-            ("f64 (emulated: int8-valued slices on bf16 tensor cores)" if precision == "ozaki" else "tf32"),
+            ("f64 (emulated: int8-valued slices on bf16 tensor cores)" if precision == "ozaki" else
+             "f32" if precision == "fp32" else "tf32"),
             "data": "synthetic",
             "config": {"workload": w.name, "path": path_taken, "precision": precision,
                        "useful_flops_per_step": useful, "n_products": st["n_products"],
                        "l2": "inputs larger than L2 (no flush)" if useful > 1e9 else "inputs in L2",
+                       **({"dense_panels": s2["dense_panels"]} if path_taken == "hybrid" else {}),
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clk.summary(), "legs_tflops": legs, "accuracy_normwise": accuracy,

@@ -81,6 +81,9 @@ typedef void (*dbcsr_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
 #define DBCSR_PREC_OZAKI 1   /* FP64 emulated with 7-bit integer slices on the tensor cores,
                                 exact integer accumulation, FP64 recombination */
 #define DBCSR_PREC_TF32  2   /* inputs rounded to TF32, FP32 accumulation (error reported only) */
+#define DBCSR_PREC_FP32  3   /* single precision (Sec. II: the library accepts single): inputs rounded
+                                to FP32, FP32 products and sums (FMA), alpha/beta in FP64; stack
+                                path only (the dense path offers TF32) */
 
 typedef struct {
     int path;          /* DBCSR_PATH_*                                        */

@@ -596,8 +596,9 @@ int stack_run(const SmmArgs& g0, int64_t b0, int64_t b1, int64_t nprod, dbcsr_ma
 int hybrid_products(const SmmArgs& g, const StackPlan& P, double* data, bool ta, bool tb, double alpha,
                     dbcsr_matrix_s* A, dbcsr_matrix_s* B, double beta, bool use_old, dbcsr_matrix_s* C,
                     const dbcsr_opts& o) {
-    if (o.precision == DBCSR_PREC_TF32)
-        return fail(DBCSR_ERR_ARG, "hybrid path: TF32 has no stack kernels; use the dense path");
+    if (o.precision == DBCSR_PREC_TF32 || o.precision == DBCSR_PREC_FP32)
+        return fail(DBCSR_ERR_ARG, "hybrid path: FP64 or emulated FP64 only (TF32 has no stack kernels, FP32 no "
+                                   "dense GEMM)");
     const int nrows = C->nbr;
     const int64_t N = C->h_coff[C->nbc];
     const int64_t K = ta ? A->h_roff[A->nbr] : A->h_coff[A->nbc];
@@ -641,9 +642,11 @@ int hybrid_products(const SmmArgs& g, const StackPlan& P, double* data, bool ta,
     DB_TRY(d2h(crp.data(), P.c_rowptr, sizeof(int) * (nrows + 1)));
     std::vector<int64_t> ps(P.nC + 1);
     DB_TRY(d2h(ps.data(), P.c_pstart, sizeof(int64_t) * (P.nC + 1)));
-    DBuf<double> dB, dA, dC;
-    bool have_b = false;
+    // stack runs first; the dense panels are gathered into one GEMM (separate
+    // panel GEMMs would each fill only part of the GPU)
     double flops = 0.0, useful_dense = 0.0;   // useful_dense: products of the dense runs
+    int64_t Md = 0;
+    std::vector<int64_t> at(runs.size(), 0);
     for (size_t q = 0; q < runs.size(); q++) {
         const int r0 = runs[q].first, r1 = runs[q].second;
         const int64_t b0 = crp[r0], b1 = crp[r1];
@@ -651,27 +654,39 @@ int hybrid_products(const SmmArgs& g, const StackPlan& P, double* data, bool ta,
             DB_TRY(stack_run(g, b0, b1, ps[b1] - ps[b0], A, ta, B, tb, C, o, &flops));
             continue;
         }
-        if (!have_b) {
-            DB_TRY(dB.alloc((size_t)std::max<int64_t>(K * N, 1)));
-            DB_TRY(densify(B, tb, dB.p, K, B->nblks != (int64_t)B->nbr * B->nbc));
-            have_b = true;
+        at[q] = Md;
+        Md += C->h_roff[r1] - C->h_roff[r0];
+        useful_dense += ps[b1] - ps[b0];
+    }
+    if (Md > 0) {
+        cudaStream_t st = g_ctx.stream;
+        DBuf<double> dB, dA, dC;
+        DB_TRY(dB.alloc((size_t)std::max<int64_t>(K * N, 1)));
+        DB_TRY(densify(B, tb, dB.p, K, B->nblks != (int64_t)B->nbr * B->nbc));
+        DB_TRY(dA.alloc((size_t)std::max<int64_t>(Md * K, 1)));
+        DB_TRY(dC.alloc((size_t)std::max<int64_t>(Md * N, 1)));
+        if (Md * K > 0) DB_CUDA(cudaMemsetAsync(dA.p, 0, sizeof(double) * (size_t)(Md * K), st));
+        if (use_old && Md * N > 0) DB_CUDA(cudaMemsetAsync(dC.p, 0, sizeof(double) * (size_t)(Md * N), st));
+        for (size_t q = 0; q < runs.size(); q++) {
+            if (!dense_run[q]) continue;
+            DB_TRY(densify_rows(A, ta, runs[q].first, runs[q].second, dA.p, Md, at[q]));
+            if (use_old) DB_TRY(densify_rows(C, false, runs[q].first, runs[q].second, dC.p, Md, at[q]));
         }
-        const int64_t Mr = C->h_roff[r1] - C->h_roff[r0];
-        DB_TRY(dA.alloc((size_t)std::max<int64_t>(Mr * K, 1)));
-        DB_TRY(dC.alloc((size_t)std::max<int64_t>(Mr * N, 1)));
-        DB_TRY(densify_rows(A, ta, r0, r1, dA.p, Mr));
-        if (use_old) DB_TRY(densify_rows(C, false, r0, r1, dC.p, Mr));
         const double beta_eff = use_old ? beta : 0.0;
         if (o.precision == DBCSR_PREC_FP64) {
-            DB_TRY(dgemm_fp64(Mr, N, K, alpha, dA.p, Mr, dB.p, K, beta_eff, dC.p, Mr));
-            flops += 2.0 * (double)Mr * (double)N * (double)K;
+            DB_TRY(dgemm_fp64(Md, N, K, alpha, dA.p, Md, dB.p, K, beta_eff, dC.p, Md));
+            flops += 2.0 * (double)Md * (double)N * (double)K;
         } else {
             double f = 0.0;
-            DB_TRY(dgemm_emulated(Mr, N, K, alpha, dA.p, Mr, dB.p, K, beta_eff, dC.p, Mr, o, &f));
+            DB_TRY(dgemm_emulated(Md, N, K, alpha, dA.p, Md, dB.p, K, beta_eff, dC.p, Md, o, &f));
             flops += f;
         }
-        useful_dense += ps[b1] - ps[b0];
-        DB_TRY(undensify_blocks(b0, b1, P.c_row, P.c_col, P.c_off, data, C, dC.p, Mr, C->h_roff[r0]));
+        for (size_t q = 0; q < runs.size(); q++) {
+            if (!dense_run[q]) continue;
+            const int r0 = runs[q].first, r1 = runs[q].second;
+            DB_TRY(undensify_blocks(crp[r0], crp[r1], P.c_row, P.c_col, P.c_off, data, C, dC.p, Md,
+                                    C->h_roff[r0] - at[q]));
+        }
     }
     // main_flops: the dense GEMMs' arithmetic, plus for FP64 stack runs their
     // products at the average useful flops per product (emulated runs report
@@ -734,6 +749,18 @@ int multiply_stacks(bool ta, bool tb, double alpha, dbcsr_matrix_s* A, dbcsr_mat
     g.alpha = alpha;
     g.beta = beta;
     g.counter = counter.p;
+    g.A32 = nullptr;
+    g.B32 = nullptr;
+    DBuf<float> a32, b32;
+    if (o.precision == DBCSR_PREC_FP32) {
+        // FP32 copies of the operands' stored data (same offsets)
+        DB_TRY(a32.alloc((size_t)std::max<int64_t>(A->nelems, 1)));
+        DB_TRY(b32.alloc((size_t)std::max<int64_t>(B->nelems, 1)));
+        DB_TRY(to_f32(A->d_data, A->nelems, a32.p));
+        DB_TRY(to_f32(B->d_data, B->nelems, b32.p));
+        g.A32 = a32.p;
+        g.B32 = b32.p;
+    }
     int rc;
     mark(1);
     if (o.path == DBCSR_PATH_HYBRID) {
@@ -741,6 +768,11 @@ int multiply_stacks(bool ta, bool tb, double alpha, dbcsr_matrix_s* A, dbcsr_mat
     } else if (o.precision == DBCSR_PREC_FP64) {
         timer_kernel_begin();
         rc = smm_fp64_dispatch(g, C->max_rs * C->max_cs, o.kernel);
+        timer_kernel_end();
+        g_stats.main_flops = g_stats.useful_flops;
+    } else if (o.precision == DBCSR_PREC_FP32) {
+        timer_kernel_begin();
+        rc = smm_fp32_dispatch(g, C->max_rs * C->max_cs);
         timer_kernel_end();
         g_stats.main_flops = g_stats.useful_flops;
     } else {
@@ -932,7 +964,7 @@ extern "C" int dbcsr_multiply(char transa, char transb, double alpha, dbcsr_matr
         return fail(DBCSR_ERR_ARG, "multiply: trans must be 'N', 'T' or 'C'");
     dbcsr_opts o{};
     if (opts) o = *opts;
-    if (o.path < 0 || o.path > 3 || o.precision < 0 || o.precision > 2 || o.ozaki_slices < 0 ||
+    if (o.path < 0 || o.path > 3 || o.precision < 0 || o.precision > 3 || o.ozaki_slices < 0 ||
         o.ozaki_slices > 12 || o.hybrid_panel < 0 || o.hybrid_fill_pct < 0 || o.hybrid_fill_pct > 100)
         return fail(DBCSR_ERR_ARG, "multiply: invalid options");
     DB_TRY(ensure_device());
@@ -947,8 +979,10 @@ extern "C" int dbcsr_multiply(char transa, char transb, double alpha, dbcsr_matr
     if (path == DBCSR_PATH_AUTO) {
         const bool a_full = A->nblks == (int64_t)A->nbr * A->nbc && A->nblks > 0;
         const bool b_full = B->nblks == (int64_t)B->nbr * B->nbc && B->nblks > 0;
-        path = (a_full && b_full) ? DBCSR_PATH_DENSE : DBCSR_PATH_STACKS;
+        path = (a_full && b_full && o.precision != DBCSR_PREC_FP32) ? DBCSR_PATH_DENSE : DBCSR_PATH_STACKS;
     }
+    if (path == DBCSR_PATH_DENSE && o.precision == DBCSR_PREC_FP32)
+        return fail(DBCSR_ERR_ARG, "multiply: FP32 runs on the stack path (the dense path offers TF32)");
     g_stats.path = path;
     g_stats.precision = o.precision;
     PhaseTimer timer;

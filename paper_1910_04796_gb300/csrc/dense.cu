@@ -193,12 +193,10 @@ int densify(const dbcsr_matrix_s* m, bool trans, double* dense, int64_t ld, bool
     return DBCSR_OK;
 }
 
-int densify_rows(const dbcsr_matrix_s* m, bool trans, int lo, int hi, double* dense, int64_t ld) {
+int densify_rows(const dbcsr_matrix_s* m, bool trans, int lo, int hi, double* dense, int64_t ld, int64_t at) {
     cudaStream_t st = ctx().stream;
     const std::vector<int64_t>& ro = trans ? m->h_coff : m->h_roff;
-    const int64_t base = ro[lo], rows = ro[hi] - base;
-    const int64_t cols = trans ? m->h_roff[m->nbr] : m->h_coff[m->nbc];
-    if (rows * cols > 0) DB_CUDA(cudaMemsetAsync(dense, 0, sizeof(double) * (size_t)(ld * (cols - 1) + rows), st));
+    const int64_t base = ro[lo] - at;   // element row ro[lo] lands on dense row `at`
     if (m->nblks == 0) return DBCSR_OK;
     int grid = (int)std::min<int64_t>(m->nblks, (int64_t)ctx().num_sms * 16);
     k_densify<<<grid, 256, 0, st>>>(m->nblks, m->d_row_of, m->d_col, m->d_off, m->d_data, m->d_rs, m->d_cs,

@@ -67,13 +67,32 @@ __device__ __forceinline__ double round_i128_scaled(__int128 S, int k) {
         mant = lo << (52 - msb);
         ex = msb - 52;
     } else {
-        const int sh = msb - 52;
-        const unsigned __int128 q = a >> sh;
-        mant = (unsigned long long)q;
-        const unsigned __int128 rem = a - (q << sh);
-        const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
-        ex = sh;
-        if (rem > half || (rem == half && (mant & 1ull))) {
+        // drop d = msb - 52 low bits; 64-bit shifts only (a variable 128-bit
+        // shift costs a branchy sequence). mant < 2^53 in both cases.
+        const int d = msb - 52;
+        bool up;
+        if (d < 64) {
+            mant = (hi << (64 - d)) | (lo >> d);
+            const unsigned long long rem = lo & ((1ull << d) - 1ull), half = 1ull << (d - 1);
+            up = rem > half || (rem == half && (mant & 1ull));
+        } else {
+            const int e = d - 64;   // 0 .. 63
+            mant = hi >> e;
+            const unsigned long long rh = e ? (hi & ((1ull << e) - 1ull)) : 0ull;
+            // half = 2^(d-1): in the high word when d > 64, else the top bit of the low word
+            bool gt, eq;
+            if (e == 0) {
+                gt = lo > (1ull << 63);
+                eq = lo == (1ull << 63);
+            } else {
+                const unsigned long long hh = 1ull << (e - 1);
+                gt = rh > hh || (rh == hh && lo != 0ull);
+                eq = rh == hh && lo == 0ull;
+            }
+            up = gt || (eq && (mant & 1ull));
+        }
+        ex = d;
+        if (up) {
             mant += 1;
             if (mant >> 53) {   // carried into a new power of two
                 mant >>= 1;

@@ -22,6 +22,8 @@ struct SmmArgs {
     const int64_t* Cold_off;
     double alpha, beta;
     unsigned long long* counter;  // zeroed work counter
+    const float* A32;          // FP32 copies of op(A)'s and op(B)'s stored data (FP32 path only)
+    const float* B32;
 };
 
 // FP64 stack-kernel variants (the autotuner's search space), see smm_fp64.cu
@@ -33,5 +35,10 @@ int smm_fp64_generic(const SmmArgs& g, int max_mn);
 int smm_fp64_dispatch(const SmmArgs& g, int max_mn, int kernel);
 // (m, n) -> variant entries of the tuning table (replaces the table)
 int smm_set_table(const int* m, const int* n, const int* variant, int count);
+
+// FP32 stack kernels over every C block (g.A32, g.B32 set), one warp per C block
+int smm_fp32_dispatch(const SmmArgs& g, int max_mn);
+// FP64 -> FP32 copy, round to nearest even
+int to_f32(const double* in, int64_t n, float* out);
 
 }  // namespace dbcsr

@@ -428,22 +428,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_smm_emul_tc(TcArgs a) {
             // first NU = min(4, s) levels and V over the rest: |U|, |V| < 2^53, so
             // both run in int64 and one 128-bit shift and add joins them.
             constexpr int NU = S < 4 ? S : 4;
+            // the four elements are computed unconditionally (independent chains
+            // the scheduler can interleave); only the stores are guarded
+            double res[TC_EL];
+#pragma unroll
+            for (int k = 0; k < TC_EL; k++) {
+                long long U = 0, V = 0;
+#pragma unroll
+                for (int d = 0; d < NU; d++) U = U * 128 + lv[d][k];
+#pragma unroll
+                for (int d = NU; d < S; d++) V = V * 128 + lv[d][k];
+                const __int128 Sx = (__int128)U * ((__int128)1 << (7 * (S - NU))) + V;
+                double v = __dmul_rn(a.alpha, emul::round_i128_scaled(Sx, ei + fj[k] - 7 * (S + 1)));
+                if (cur.old_off >= 0) v = __dadd_rn(v, __dmul_rn(a.beta, oldv[k]));
+                res[k] = v;
+            }
             if (row_ok) {
                 double* cout = a.Cd + cur.c_off;
 #pragma unroll
                 for (int k = 0; k < TC_EL; k++) {
                     const int j = TC_EL * ep + k;
-                    if (j < cur.n) {
-                        long long U = 0, V = 0;
-#pragma unroll
-                        for (int d = 0; d < NU; d++) U = U * 128 + lv[d][k];
-#pragma unroll
-                        for (int d = NU; d < S; d++) V = V * 128 + lv[d][k];
-                        const __int128 Sx = (__int128)U * ((__int128)1 << (7 * (S - NU))) + V;
-                        double v = __dmul_rn(a.alpha, emul::round_i128_scaled(Sx, ei + fj[k] - 7 * (S + 1)));
-                        if (cur.old_off >= 0) v = __dadd_rn(v, __dmul_rn(a.beta, oldv[k]));
-                        cout[(int64_t)j * cur.m + i] = v;
-                    }
+                    if (j < cur.n) cout[(int64_t)j * cur.m + i] = res[k];
                 }
             }
         }

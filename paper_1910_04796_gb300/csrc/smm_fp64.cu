@@ -61,15 +61,17 @@ __device__ __forceinline__ void team_sync(int team) {
 }
 
 // one team per C block; each lane holds up to Q elements e = lane + 32*q,
-// r = e % m, c = e / m (column-major order within the block)
-template <int Q, int TA, int TB, int W>
-__global__ void __launch_bounds__(256) k_smm_fp64(SmmArgs g, const uint32_t* __restrict__ list, int64_t nlist,
-                                                        int chunk) {
+// r = e % m, c = e / m (column-major order within the block). T is the
+// arithmetic type: double (FP64 path) or float (FP32 path: operands read from
+// FP32 copies of A and B, FP32 FMA sums, alpha/beta applied in FP64).
+template <typename T, int Q, int TA, int TB, int W>
+__device__ __forceinline__ void smm_body(const SmmArgs& g, const T* __restrict__ adata, const T* __restrict__ bdata,
+                                         const uint32_t* __restrict__ list, int64_t nlist, int chunk,
+                                         double* s_red) {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int team = warp / W, tw = warp % W;        // team in CTA, warp in team
     __shared__ int s_cb[8];
-    extern __shared__ double s_red[];                 // [teams][W-1][Q][32] partial sums
     for (;;) {
         // a team takes 32 consecutive C blocks at a time; lane t fetches block
         // t's index data in parallel, then the blocks are processed in order
@@ -100,11 +102,11 @@ __global__ void __launch_bounds__(256) k_smm_fp64(SmmArgs g, const uint32_t* __r
         const double* cold = (old_off >= 0) ? g.Cold + old_off : nullptr;
         for (int e0 = 0; e0 < mn; e0 += 32 * Q) {
             const int nq = min(Q, (mn - e0 + 31) >> 5);
-            double acc[Q];
+            T acc[Q];
             int ro[Q], co[Q];
 #pragma unroll
             for (int q = 0; q < Q; q++) {
-                acc[q] = 0.0;
+                acc[q] = T(0);
                 int e = e0 + lane + 32 * q;
                 if (e >= mn) e = 0;
                 ro[q] = e % m;
@@ -119,7 +121,7 @@ __global__ void __launch_bounds__(256) k_smm_fp64(SmmArgs g, const uint32_t* __r
                 if (pj < p1) {
                     const int2 pr = g.prod[pj];
                     my_ao = g.A.off[pr.x];
-                    my_kk = (int)((g.A.off[pr.x + 1] - my_ao) / m);
+                    my_kk = (int)(g.A.off[pr.x + 1] - my_ao) / m;   // block sizes < 2^31: 32-bit division
                     my_bo = g.B.off[pr.y];
                 }
                 const int nb = (int)min((int64_t)32, (p1 - pb + W - 1) / W);
@@ -127,8 +129,8 @@ __global__ void __launch_bounds__(256) k_smm_fp64(SmmArgs g, const uint32_t* __r
                     const long long ao = __shfl_sync(0xffffffffu, my_ao, t);
                     const long long bo = __shfl_sync(0xffffffffu, my_bo, t);
                     const int kk = __shfl_sync(0xffffffffu, my_kk, t);
-                    const double* __restrict__ a = g.A.data + ao;
-                    const double* __restrict__ b = g.B.data + bo;
+                    const T* __restrict__ a = adata + ao;
+                    const T* __restrict__ b = bdata + bo;
                     int aidx[Q], bidx[Q];
 #pragma unroll
                     for (int q = 0; q < Q; q++) {
@@ -149,7 +151,7 @@ __global__ void __launch_bounds__(256) k_smm_fp64(SmmArgs g, const uint32_t* __r
             }
             if (W > 1) {
                 // partial sums of warps 1..W-1 to shared memory, added in warp order by warp 0
-                double* red = s_red + (size_t)team * (W - 1) * Q * 32;
+                T* red = reinterpret_cast<T*>(s_red) + (size_t)team * (W - 1) * Q * 32;
                 if (tw > 0) {
 #pragma unroll
                     for (int q = 0; q < Q; q++) red[((tw - 1) * Q + q) * 32 + lane] = acc[q];
@@ -167,7 +169,7 @@ __global__ void __launch_bounds__(256) k_smm_fp64(SmmArgs g, const uint32_t* __r
                 for (int q = 0; q < Q; q++) {
                     const int e = e0 + lane + 32 * q;
                     if (q < nq && e < mn) {
-                        double v = __dmul_rn(g.alpha, acc[q]);
+                        double v = __dmul_rn(g.alpha, (double)acc[q]);
                         if (cold) v = __dadd_rn(v, __dmul_rn(g.beta, cold[e]));
                         cout[e] = v;
                     }
@@ -175,6 +177,54 @@ __global__ void __launch_bounds__(256) k_smm_fp64(SmmArgs g, const uint32_t* __r
             }
         }
         }   // blocks of the batch
+    }
+}
+
+template <int Q, int TA, int TB, int W>
+__global__ void __launch_bounds__(256) k_smm_fp64(SmmArgs g, const uint32_t* __restrict__ list, int64_t nlist,
+                                                        int chunk) {
+    extern __shared__ double s_red[];                 // [teams][W-1][Q][32] partial sums
+    smm_body<double, Q, TA, TB, W>(g, g.A.data, g.B.data, list, nlist, chunk, s_red);
+}
+
+// FP32 stack kernel: one warp per C block
+template <int Q, int TA, int TB>
+__global__ void __launch_bounds__(256) k_smm_fp32(SmmArgs g, const uint32_t* __restrict__ list, int64_t nlist,
+                                                        int chunk) {
+    smm_body<float, Q, TA, TB, 1>(g, g.A32, g.B32, list, nlist, chunk, nullptr);
+}
+
+// FP64 -> FP32, round to nearest even
+__global__ void k_to_f32(int64_t n, const double* __restrict__ in, float* __restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = __double2float_rn(in[i]);
+}
+
+template <int Q>
+int launch_fp32_q(const SmmArgs& g, const uint32_t* list, int64_t nlist) {
+    cudaStream_t st = ctx().stream;
+    const int threads = 256, teams_per_cta = 8;
+    int grid = ctx().num_sms * (2048 / threads);
+    if ((int64_t)grid * teams_per_cta > nlist) grid = (int)cdiv(nlist, teams_per_cta);
+    if (grid < 1) return DBCSR_OK;
+    const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(32, nlist / ((int64_t)grid * teams_per_cta * 4)));
+    const int ta = g.A.trans, tb = g.B.trans;
+    if (!ta && !tb) k_smm_fp32<Q, 0, 0><<<grid, threads, 0, st>>>(g, list, nlist, chunk);
+    else if (ta && !tb) k_smm_fp32<Q, 1, 0><<<grid, threads, 0, st>>>(g, list, nlist, chunk);
+    else if (!ta && tb) k_smm_fp32<Q, 0, 1><<<grid, threads, 0, st>>>(g, list, nlist, chunk);
+    else k_smm_fp32<Q, 1, 1><<<grid, threads, 0, st>>>(g, list, nlist, chunk);
+    DB_KCHECK();
+    return DBCSR_OK;
+}
+
+int launch_fp32(const SmmArgs& g, int qidx, const uint32_t* list, int64_t nlist) {
+    switch (qidx) {
+        case 0: return launch_fp32_q<1>(g, list, nlist);
+        case 1: return launch_fp32_q<2>(g, list, nlist);
+        case 2: return launch_fp32_q<4>(g, list, nlist);
+        case 3: return launch_fp32_q<8>(g, list, nlist);
+        case 4: return launch_fp32_q<16>(g, list, nlist);
+        default: return launch_fp32_q<32>(g, list, nlist);
     }
 }
 
@@ -319,6 +369,51 @@ int smm_fp64_dispatch(const SmmArgs& g, int max_mn, int kernel) {
         SmmArgs gk = g;
         gk.counter = ctr.p + k;
         DB_TRY(launch_group(gk, k / NQ, k % NQ, idx.p + start, h_counts[k]));
+        start += h_counts[k];
+    }
+    return DBCSR_OK;
+}
+
+int to_f32(const double* in, int64_t n, float* out) {
+    if (n <= 0) return DBCSR_OK;
+    const int grid = (int)std::min<int64_t>(cdiv(n, 256), (int64_t)ctx().num_sms * 32);
+    k_to_f32<<<grid, 256, 0, ctx().stream>>>(n, in, out);
+    DB_KCHECK();
+    return DBCSR_OK;
+}
+
+// FP32 stack kernels: C blocks grouped by elements-per-lane class, one warp each.
+int smm_fp32_dispatch(const SmmArgs& g, int max_mn) {
+    if (g.nC == 0) return DBCSR_OK;
+    if (g.nC >= INT32_MAX) return fail(DBCSR_ERR_OVERFLOW, "stack kernels: too many C blocks");
+    cudaStream_t st = ctx().stream;
+    DBuf<uint32_t> key, idx;
+    DBuf<int> counts;
+    DB_TRY(key.alloc(g.nC));
+    DB_TRY(idx.alloc(g.nC));
+    DB_TRY(counts.alloc(NQ));
+    DB_CUDA(cudaMemsetAsync(counts.p, 0, sizeof(int) * NQ, st));
+    k_classify<<<(unsigned)cdiv(g.nC, 256), 256, 0, st>>>(g.nC, g.c_row, g.c_col, g.c_pstart, g.rsC, g.csC, nullptr,
+                                                          TDIM, 0, key.p, idx.p, counts.p);
+    DB_KCHECK();
+    std::vector<int> h_counts(NQ);
+    DB_CUDA(cudaMemcpyAsync(h_counts.data(), counts.p, sizeof(int) * NQ, cudaMemcpyDeviceToHost, st));
+    DB_CUDA(cudaStreamSynchronize(st));
+    int used = 0, only = 0;
+    for (int k = 0; k < NQ; k++)
+        if (h_counts[k]) { used++; only = k; }
+    (void)max_mn;
+    if (used <= 1) return launch_fp32(g, only, nullptr, g.nC);
+    DB_TRY(radix_sort_u32(key.p, idx.p, g.nC, 8));
+    DBuf<unsigned long long> ctr;
+    DB_TRY(ctr.alloc(NQ));
+    DB_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(unsigned long long) * NQ, st));
+    int64_t start = 0;
+    for (int k = 0; k < NQ; k++) {
+        if (!h_counts[k]) continue;
+        SmmArgs gk = g;
+        gk.counter = ctr.p + k;
+        DB_TRY(launch_fp32(gk, k, idx.p + start, h_counts[k]));
         start += h_counts[k];
     }
     return DBCSR_OK;

@@ -17,8 +17,8 @@ from . import build as _build
 OK = 0
 ERR_ARG, ERR_DIM, ERR_ALLOC, ERR_OVERFLOW, ERR_TIMEOUT, ERR_CUDA, ERR_STATE = -1, -2, -3, -4, -5, -6, -7
 PATH_AUTO, PATH_STACKS, PATH_DENSE, PATH_HYBRID = 0, 1, 2, 3
-PREC_FP64, PREC_OZAKI, PREC_TF32 = 0, 1, 2
-_PREC = {"fp64": PREC_FP64, "ozaki": PREC_OZAKI, "tf32": PREC_TF32}
+PREC_FP64, PREC_OZAKI, PREC_TF32, PREC_FP32 = 0, 1, 2, 3
+_PREC = {"fp64": PREC_FP64, "ozaki": PREC_OZAKI, "tf32": PREC_TF32, "fp32": PREC_FP32}
 _PATH = {"auto": PATH_AUTO, "stacks": PATH_STACKS, "dense": PATH_DENSE, "hybrid": PATH_HYBRID}
 
 
@@ -302,7 +302,7 @@ def has_precision(name: str) -> bool:
     return name in _AVAILABLE
 
 
-_AVAILABLE = {"fp64", "ozaki", "tf32"}
+_AVAILABLE = {"fp64", "ozaki", "tf32", "fp32"}
 
 
 def dgemm_emulated_noalloc(alpha, A, B, beta, Cmat, slices=0, stream=None):

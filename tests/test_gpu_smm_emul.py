@@ -100,3 +100,24 @@ def test_emulated_stacks_reject_large_blocks():
     with pytest.raises(dbcsr.DbcsrError) as e:
         gpu_multiply("N", "N", 1.0, A, B, 0.0, path="stacks", precision="ozaki")
     assert e.value.code == dbcsr.ERR_ARG
+
+
+@pytest.mark.parametrize("kernel", KERNELS)
+def test_rounding_ties_to_even(kernel):
+    # dot products 2^53 + odd and 2^54 + 2 mod 4: halfway between two doubles;
+    # the exact integer sum is rounded once, to even. Every operand bit lies in
+    # slices 1 and 4 (7 slices of 7 bits below the row / column maximum), so
+    # no slice pair is truncated and the emulation is the exact dot product.
+    from fractions import Fraction
+    a_rows = [(2.0 ** 27, 1.0), (2.0 ** 27, 3.0), (-(2.0 ** 27), 1.0), (2.0 ** 28, 2.0)]
+    b_cols = [(2.0 ** 26, 1.0), (2.0 ** 26, -1.0), (2.0 ** 26, 3.0)]
+    Ablk = np.array(a_rows)                    # 4 x 2
+    Bblk = np.array(b_cols).T                  # 2 x 3
+    one = np.array([0], np.int32)
+    A = synth.BlockSparse(np.array([4], np.int32), np.array([2], np.int32), one, one, Ablk.reshape(-1, order="F"))
+    B = synth.BlockSparse(np.array([2], np.int32), np.array([3], np.int32), one, one, Bblk.reshape(-1, order="F"))
+    got, _ = gpu_multiply("N", "N", 1.0, A, B, 0.0, path="stacks", precision="ozaki", kernel=kernel)
+    ref, _, _ = emul_ref("N", "N", A, B, None, 1.0, 0.0, 7)
+    assert np.array_equal(got.data, ref.data)
+    exact = [[float(sum(Fraction(x) * Fraction(y) for x, y in zip(r, c))) for c in b_cols] for r in a_rows]
+    assert np.array_equal(got.data.reshape((4, 3), order="F"), np.array(exact))
