@@ -35,6 +35,8 @@ from . import dbcsr, synth
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_TABLE = os.path.join(HERE, "tuning", "gb300_fp64.json")
+# every (m, n) up to 32 predicted by the regression-tree model from a 20 % sample
+MODEL_TABLE = os.path.join(HERE, "tuning", "gb300_fp64_model.json")
 
 
 def _case(m, n, ksizes, seed, nb=48, p=0.5):
@@ -112,13 +114,18 @@ def tune(msizes, nsizes, ksizes, reps=3):
     return entries
 
 
-def load_table(path=DEFAULT_TABLE) -> bool:
-    """Hand a tuned table to the library; False if the file does not exist."""
-    if not os.path.exists(path):
+def load_table(path=DEFAULT_TABLE, model_path=MODEL_TABLE) -> bool:
+    """Hand the tuning table to the library: the model's predictions for every
+    (m, n), overridden by the shapes that were timed; False if neither exists."""
+    entries = {}
+    for p in (model_path, path):
+        if p and os.path.exists(p):
+            with open(p) as f:
+                for e in json.load(f)["entries"]:
+                    entries[(int(e[0]), int(e[1]))] = int(e[2])
+    if not entries:
         return False
-    with open(path) as f:
-        t = json.load(f)
-    dbcsr.set_tuning([(e[0], e[1], e[2]) for e in t["entries"]])
+    dbcsr.set_tuning([(m, n, v) for (m, n), v in sorted(entries.items())])
     return True
 
 
