@@ -259,6 +259,9 @@ def main():
     ap.add_argument("--path", default="auto", choices=["auto", "stacks", "dense", "hybrid"])
     ap.add_argument("--slices", type=int, default=0)
     ap.add_argument("--occ", type=float, default=0.1, help="block occupancy of the 'occupancy' workload")
+    ap.add_argument("--hybrid-panel", type=int, default=-1,
+                    help="block rows per panel on the hybrid path (-1: the workload's panel height, else automatic)")
+    ap.add_argument("--hybrid-fill", type=int, default=0, help="densify panels at least this %% occupied (0: 50)")
     ap.add_argument("--kernel", type=int, default=0,
                     help="stack kernel choice passed to dbcsr_multiply (0 = automatic)")
     ap.add_argument("--ref-rows", type=int, default=48, help="C block rows per oracle sample")
@@ -294,9 +297,12 @@ def main():
     else:
         Cm = dbcsr.Matrix.create(rs, cs, np.zeros(0, np.int32), np.zeros(0, np.int32))
 
+    hpanel = args.hybrid_panel if args.hybrid_panel >= 0 else int(w.extra.get("panel", 0))
+
     def step(prec=precision, path=args.path, timing=False):
         dbcsr.multiply(w.transa, w.transb, w.alpha, A, B, w.beta, Cm, path=path, precision=prec,
-                       ozaki_slices=args.slices, kernel=args.kernel, timing=timing)
+                       ozaki_slices=args.slices, kernel=args.kernel, timing=timing, hybrid_panel=hpanel,
+                       hybrid_fill_pct=args.hybrid_fill)
 
     step()
     st = dbcsr.stats()
