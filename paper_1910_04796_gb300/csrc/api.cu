@@ -647,16 +647,29 @@ int hybrid_products(const SmmArgs& g, const StackPlan& P, double* data, bool ta,
     double flops = 0.0, useful_dense = 0.0;   // useful_dense: products of the dense runs
     int64_t Md = 0;
     std::vector<int64_t> at(runs.size(), 0);
+    CRanges sparse;
+    int64_t sparse_prod = 0;
     for (size_t q = 0; q < runs.size(); q++) {
         const int r0 = runs[q].first, r1 = runs[q].second;
         const int64_t b0 = crp[r0], b1 = crp[r1];
         if (!dense_run[q]) {
-            DB_TRY(stack_run(g, b0, b1, ps[b1] - ps[b0], A, ta, B, tb, C, o, &flops));
+            if (o.precision == DBCSR_PREC_FP64) {
+                DB_TRY(stack_run(g, b0, b1, ps[b1] - ps[b0], A, ta, B, tb, C, o, &flops));
+            } else {
+                sparse.push_back({b0, b1});   // emulated: one call, operands sliced once
+                sparse_prod += ps[b1] - ps[b0];
+            }
             continue;
         }
         at[q] = Md;
         Md += C->h_roff[r1] - C->h_roff[r0];
         useful_dense += ps[b1] - ps[b0];
+    }
+    if (!sparse.empty()) {
+        double f = 0.0;
+        DB_CUDA(cudaMemsetAsync(g.counter, 0, sizeof(unsigned long long), g_ctx.stream));
+        DB_TRY(smm_emulated(g, A, ta, B, tb, C, o, sparse_prod, &f, &sparse));
+        flops += f;
     }
     if (Md > 0) {
         cudaStream_t st = g_ctx.stream;
@@ -772,7 +785,8 @@ int multiply_stacks(bool ta, bool tb, double alpha, dbcsr_matrix_s* A, dbcsr_mat
         g_stats.main_flops = g_stats.useful_flops;
     } else if (o.precision == DBCSR_PREC_FP32) {
         timer_kernel_begin();
-        rc = smm_fp32_dispatch(g, C->max_rs * C->max_cs);
+        rc = smm_fp32_dispatch(g, C->max_rs * C->max_cs,
+                               std::max(std::max(A->max_rs, A->max_cs), std::max(B->max_rs, B->max_cs)));
         timer_kernel_end();
         g_stats.main_flops = g_stats.useful_flops;
     } else {

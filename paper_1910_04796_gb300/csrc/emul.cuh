@@ -18,8 +18,10 @@ int dgemm_tf32(int64_t M, int64_t N, int64_t K, double alpha, const double* A, i
 // Stack path in emulated FP64 (same contract as smm_fp64_generic); A, B are
 // the stored operands (op() given by ta, tb), C the result matrix whose sizes
 // and offsets describe the new blocks. Blocks up to 32 x 32. nprod: products
-// of the plan; main_flops (optional): tensor-core arithmetic issued.
+// computed; main_flops (optional): tensor-core arithmetic issued. ranges
+// (optional): only the plan's C blocks [first, second) of each range (the
+// operands are cut into slices once for all of them).
 int smm_emulated(const SmmArgs& g, dbcsr_matrix_s* A, bool ta, dbcsr_matrix_s* B, bool tb, dbcsr_matrix_s* C,
-                 const dbcsr_opts& o, int64_t nprod, double* main_flops);
+                 const dbcsr_opts& o, int64_t nprod, double* main_flops, const CRanges* ranges = nullptr);
 
 }  // namespace dbcsr

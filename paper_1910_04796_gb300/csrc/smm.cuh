@@ -1,5 +1,8 @@
 // smm.cuh -- arguments of the batched small-matrix product kernels.
 #pragma once
+#include <utility>
+#include <vector>
+
 #include "internal.cuh"
 
 namespace dbcsr {
@@ -26,6 +29,9 @@ struct SmmArgs {
     const float* B32;
 };
 
+// ranges [first, second) of a plan's C blocks
+using CRanges = std::vector<std::pair<int64_t, int64_t>>;
+
 // FP64 stack-kernel variants (the autotuner's search space), see smm_fp64.cu
 constexpr int SMM_NUM_VARIANTS = 4;
 
@@ -36,8 +42,9 @@ int smm_fp64_dispatch(const SmmArgs& g, int max_mn, int kernel);
 // (m, n) -> variant entries of the tuning table (replaces the table)
 int smm_set_table(const int* m, const int* n, const int* variant, int count);
 
-// FP32 stack kernels over every C block (g.A32, g.B32 set), one warp per C block
-int smm_fp32_dispatch(const SmmArgs& g, int max_mn);
+// FP32 stack kernels over every C block (g.A32, g.B32 set), one warp per C
+// block; max_edge: the largest block edge of op(A) and op(B)
+int smm_fp32_dispatch(const SmmArgs& g, int max_mn, int max_edge);
 // FP64 -> FP32 copy, round to nearest even
 int to_f32(const double* in, int64_t n, float* out);
 

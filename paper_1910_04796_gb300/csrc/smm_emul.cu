@@ -364,7 +364,7 @@ int line_exponents(dbcsr_matrix_s* M, bool x_is_row, int64_t nlines, DBuf<int>& 
 }  // namespace
 
 int smm_emulated(const SmmArgs& g, dbcsr_matrix_s* A, bool ta, dbcsr_matrix_s* B, bool tb, dbcsr_matrix_s* C,
-                 const dbcsr_opts& o, int64_t nprod, double* main_flops) {
+                 const dbcsr_opts& o, int64_t nprod, double* main_flops, const CRanges* ranges) {
     if (o.precision != DBCSR_PREC_OZAKI)
         return fail(DBCSR_ERR_ARG, "the stack path runs in FP64 or emulated FP64; TF32 needs the dense path");
     const int s = o.ozaki_slices > 0 ? o.ozaki_slices : 7;
@@ -393,15 +393,17 @@ int smm_emulated(const SmmArgs& g, dbcsr_matrix_s* A, bool ta, dbcsr_matrix_s* B
     DBuf<int> e, f;
     DB_TRY(line_exponents(A, !ta, Mop, e));
     DB_TRY(line_exponents(B, tb, Nop, f));
-    // kernel: 0 = tcgen05 when every block edge is at least 24 (padding to
-    // 32 x 32 costs at most 2.4x), else mma.sync; 1 = mma.sync; 2 = tcgen05
+    // kernel: 0 = tcgen05 when every block edge is at least 12, else mma.sync;
+    // 1 = mma.sync; 2 = tcgen05. Measured on GB300: 22 x 22 blocks padded to
+    // 32 x 32 run 5.8x faster on tcgen05; mixed 5..32 blocks slightly faster
+    // on mma.sync (padding to 16 instead of 32)
     int kmin = 1 << 30;
     for (const std::vector<int>* v : {&A->h_rs, &A->h_cs, &B->h_rs, &B->h_cs})
         for (int x : *v) kmin = std::min(kmin, x);
     const bool tc_ok = smm_emul_tc_usable();
     if (o.kernel == 2 && !tc_ok) return fail(DBCSR_ERR_STATE, "tcgen05 emulated stack kernel unavailable");
-    if (o.kernel == 2 || (o.kernel == 0 && kmin >= 24 && tc_ok))
-        return smm_emul_tc(g, A, ta, B, tb, C, e.p, f.p, s, nprod, main_flops);
+    if (o.kernel == 2 || (o.kernel == 0 && kmin >= 12 && tc_ok))
+        return smm_emul_tc(g, A, ta, B, tb, C, e.p, f.p, s, nprod, main_flops, ranges);
     DBuf<int64_t> soffA, soffB;
     DBuf<__nv_bfloat16> SA, SB;
     int64_t totA = 0, totB = 0;
@@ -435,19 +437,34 @@ int smm_emulated(const SmmArgs& g, dbcsr_matrix_s* A, bool ta, dbcsr_matrix_s* B
     a.beta = g.beta;
     a.flush_every = std::max(1, 1040 / (s * kp));
     a.counter = g.counter;
-    int grid = ctx().num_sms * 4;
-    if (grid > g.nC) grid = (int)g.nC;
+    // one launch per C-block range (all C blocks when no ranges are given)
+    const CRanges all{{0, g.nC}};
+    const CRanges& rr = ranges ? *ranges : all;
+    int rc = DBCSR_OK;
     timer_kernel_begin();
-    int rc;
-    switch (s) {
-        case 1: rc = launch_se<1>(a, grid); break;
-        case 2: rc = launch_se<2>(a, grid); break;
-        case 3: rc = launch_se<3>(a, grid); break;
-        case 4: rc = launch_se<4>(a, grid); break;
-        case 5: rc = launch_se<5>(a, grid); break;
-        case 6: rc = launch_se<6>(a, grid); break;
-        case 7: rc = launch_se<7>(a, grid); break;
-        default: rc = launch_se<8>(a, grid); break;
+    for (const auto& r : rr) {
+        if (r.second <= r.first) continue;
+        SeArgs ar = a;
+        ar.nC = r.second - r.first;
+        ar.c_row += r.first;
+        ar.c_col += r.first;
+        ar.c_off += r.first;
+        if (ar.c_old) ar.c_old += r.first;
+        ar.c_pstart += r.first;
+        DB_CUDA(cudaMemsetAsync(ar.counter, 0, sizeof(unsigned long long), st));
+        int grid = ctx().num_sms * 4;
+        if (grid > ar.nC) grid = (int)ar.nC;
+        switch (s) {
+            case 1: rc = launch_se<1>(ar, grid); break;
+            case 2: rc = launch_se<2>(ar, grid); break;
+            case 3: rc = launch_se<3>(ar, grid); break;
+            case 4: rc = launch_se<4>(ar, grid); break;
+            case 5: rc = launch_se<5>(ar, grid); break;
+            case 6: rc = launch_se<6>(ar, grid); break;
+            case 7: rc = launch_se<7>(ar, grid); break;
+            default: rc = launch_se<8>(ar, grid); break;
+        }
+        if (rc) break;
     }
     timer_kernel_end();
     if (rc) return rc;

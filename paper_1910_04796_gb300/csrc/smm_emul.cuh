@@ -43,6 +43,7 @@ inline SliceGeom slice_geom(dbcsr_matrix_s* M, bool x_is_row) {
 // receives the tensor-core arithmetic issued (padded operand shapes).
 bool smm_emul_tc_usable();
 int smm_emul_tc(const SmmArgs& g, dbcsr_matrix_s* A, bool ta, dbcsr_matrix_s* B, bool tb, dbcsr_matrix_s* C,
-                const int* e, const int* f, int s, int64_t nprod, double* issued_flops);
+                const int* e, const int* f, int s, int64_t nprod, double* issued_flops,
+                const CRanges* ranges = nullptr);
 
 }  // namespace dbcsr

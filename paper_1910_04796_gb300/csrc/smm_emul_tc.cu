@@ -158,12 +158,14 @@ __global__ void k_tc_slice(SliceGeom G, const int* __restrict__ ex, int s, int i
 }
 
 // traversal key of each C block: its tile, row-major over tiles
-__global__ void k_tile_keys(int64_t nC, const int* __restrict__ c_row, const int* __restrict__ c_col,
+// (C blocks first .. first + n - 1 of the plan)
+__global__ void k_tile_keys(int64_t n, int64_t first, const int* __restrict__ c_row, const int* __restrict__ c_col,
                             int tiles_c, uint32_t* __restrict__ key, uint32_t* __restrict__ idx) {
-    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (b >= nC) return;
-    key[b] = (uint32_t)(c_row[b] / TC_TILE) * (uint32_t)tiles_c + (uint32_t)(c_col[b] / TC_TILE);
-    idx[b] = (uint32_t)b;
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const int64_t b = first + q;
+    key[q] = (uint32_t)(c_row[b] / TC_TILE) * (uint32_t)tiles_c + (uint32_t)(c_col[b] / TC_TILE);
+    idx[q] = (uint32_t)b;
 }
 
 __global__ void k_tc_sched(int64_t nC, const uint32_t* __restrict__ order, const int* __restrict__ c_row,
@@ -486,7 +488,7 @@ bool smm_emul_tc_usable() {
 }
 
 int smm_emul_tc(const SmmArgs& g, dbcsr_matrix_s* A, bool ta, dbcsr_matrix_s* B, bool tb, dbcsr_matrix_s* C,
-                const int* e, const int* f, int s, int64_t nprod, double* issued_flops) {
+                const int* e, const int* f, int s, int64_t nprod, double* issued_flops, const CRanges* ranges) {
     cudaStream_t st = ctx().stream;
     DBuf<uint8_t> SA, SB;
     DB_TRY(SA.alloc((size_t)(A->nblks ? A->nblks : 1) * s * TC_SLOT));
@@ -500,25 +502,38 @@ int smm_emul_tc(const SmmArgs& g, dbcsr_matrix_s* A, bool ta, dbcsr_matrix_s* B,
         k_tc_slice<<<(int)std::min<int64_t>(cdiv(B->nblks, 8), sgrid), 256, 0, st>>>(slice_geom(B, tb), f, s, 0, SB.p);
         DB_KCHECK();
     }
-    // tile order (stable: row-major within a tile, as the C blocks are stored)
+    // the C blocks to compute (all, or the given ranges), in tile order
+    // (stable: row-major within a tile, as the C blocks are stored)
     if (g.nC >= (int64_t)UINT32_MAX) return fail(DBCSR_ERR_OVERFLOW, "emulated stack kernel: too many C blocks");
+    const CRanges all{{0, g.nC}};
+    const CRanges& rr = ranges ? *ranges : all;
+    int64_t nsel = 0;
+    for (const auto& r : rr) nsel += std::max<int64_t>(0, r.second - r.first);
+    if (nsel == 0) return DBCSR_OK;
     DBuf<uint32_t> key, order;
-    DB_TRY(key.alloc(g.nC));
-    DB_TRY(order.alloc(g.nC));
+    DB_TRY(key.alloc(nsel));
+    DB_TRY(order.alloc(nsel));
     const int tiles_r = (int)cdiv(C->nbr, TC_TILE), tiles_c = (int)cdiv(C->nbc, TC_TILE);
-    k_tile_keys<<<(unsigned)cdiv(g.nC, 256), 256, 0, st>>>(g.nC, g.c_row, g.c_col, tiles_c, key.p, order.p);
-    DB_KCHECK();
+    int64_t at = 0;
+    for (const auto& r : rr) {
+        const int64_t n = r.second - r.first;
+        if (n <= 0) continue;
+        k_tile_keys<<<(unsigned)cdiv(n, 256), 256, 0, st>>>(n, r.first, g.c_row, g.c_col, tiles_c, key.p + at,
+                                                            order.p + at);
+        DB_KCHECK();
+        at += n;
+    }
     int bits = 0;
     while (bits < 32 && ((uint64_t)1 << bits) < (uint64_t)tiles_r * tiles_c) bits++;
-    DB_TRY(radix_sort_u32(key.p, order.p, g.nC, bits));
+    DB_TRY(radix_sort_u32(key.p, order.p, nsel, bits));
     DBuf<TcBlk> sched;
-    DB_TRY(sched.alloc(g.nC));
-    k_tc_sched<<<(unsigned)cdiv(g.nC, 256), 256, 0, st>>>(g.nC, order.p, g.c_row, g.c_col, g.c_pstart, g.c_off,
+    DB_TRY(sched.alloc(nsel));
+    k_tc_sched<<<(unsigned)cdiv(nsel, 256), 256, 0, st>>>(nsel, order.p, g.c_row, g.c_col, g.c_pstart, g.c_off,
                                                           g.c_old, g.Cold_off, g.rsC, g.csC, C->d_roff, C->d_coff,
                                                           sched.p);
     DB_KCHECK();
     TcArgs a;
-    a.nC = g.nC;
+    a.nC = nsel;
     a.sched = sched.p;
     a.prod = g.prod;
     a.e = e;
@@ -531,7 +546,7 @@ int smm_emul_tc(const SmmArgs& g, dbcsr_matrix_s* A, bool ta, dbcsr_matrix_s* B,
     a.beta = g.beta;
     a.err = ctx().d_flags;
     DB_CUDA(cudaMemsetAsync(a.err, 0, sizeof(int), st));
-    const int grid = (int)std::min<int64_t>(g.nC, ctx().num_sms);
+    const int grid = (int)std::min<int64_t>(nsel, ctx().num_sms);
     int rc;
     double per = 0.0;
     timer_kernel_begin();

@@ -194,6 +194,101 @@ __global__ void __launch_bounds__(256) k_smm_fp32(SmmArgs g, const uint32_t* __r
     smm_body<float, Q, TA, TB, 1>(g, g.A32, g.B32, list, nlist, chunk, nullptr);
 }
 
+// FP32 stack kernel for blocks up to 32 x 32: a warp per C block; each
+// product's op(A) and op(B) blocks are staged in the warp's shared memory and
+// lane j accumulates column j of the C block: per inner index l, one
+// conflict-free load of B(l, j) and broadcast 16-byte loads of A(:, l) feed
+// m FMAs. FMA order per element: products in plan order, l ascending.
+// Rows m..m+3 of a partial float4 read stale values into accumulators that
+// are never stored.
+constexpr int F32_WARPS = 8;
+constexpr int F32_BSTRIDE = 33;   // sB[j * 33 + l]: lanes j read distinct banks
+constexpr int F32_ASTRIDE = 36;   // sA[l * 36 + i]: 16-byte aligned columns, transposed writes 4-way at most
+
+constexpr int F32_WARP_FLOATS = 32 * F32_ASTRIDE + 32 * F32_BSTRIDE + 32;   // A, B (+ pad to 16 bytes)
+constexpr int F32_SMEM = F32_WARPS * F32_WARP_FLOATS * (int)sizeof(float);
+
+template <int TA, int TB>
+__global__ void __launch_bounds__(32 * F32_WARPS) k_smm_f32_tile(SmmArgs g, int chunk) {
+    extern __shared__ __align__(16) float f32_smem[];
+    __shared__ int s_cb[F32_WARPS];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float* a_s = f32_smem + warp * F32_WARP_FLOATS;   // A(i, l) at l * 36 + i
+    float* b_s = a_s + 32 * F32_ASTRIDE;               // B(l, j) at j * 33 + l
+    for (;;) {
+        if (lane == 0) s_cb[warp] = (int)atomicAdd(g.counter, (unsigned long long)chunk);
+        __syncwarp();
+        const int64_t base = s_cb[warp];
+        __syncwarp();
+        if (base >= g.nC) break;
+        const int64_t cend = min(base + (int64_t)chunk, g.nC);
+        for (int64_t cb = base; cb < cend; cb++) {
+            const int m = g.rsC[g.c_row[cb]], n = g.csC[g.c_col[cb]];
+            const int64_t p0 = g.c_pstart[cb], p1 = g.c_pstart[cb + 1];
+            float acc[32];
+#pragma unroll
+            for (int i = 0; i < 32; i++) acc[i] = 0.f;
+            for (int64_t p = p0; p < p1; p++) {
+                const int2 pr = g.prod[p];
+                const int64_t ao = g.A.off[pr.x], bo = g.B.off[pr.y];
+                const int kk = (int)(g.A.off[pr.x + 1] - ao) / m;
+                const float* ga = g.A32 + ao;
+                const float* gb = g.B32 + bo;
+                __syncwarp();   // the previous product's operands are consumed
+                // op(A) is m x kk: element (i, l) of the stored block is at
+                // i + l*m (TA = 0) or l + i*kk (TA = 1); the lane runs along the
+                // contiguous index, so the reads are coalesced
+                if (!TA) {
+                    if (lane < m)
+                        for (int l = 0; l < kk; l++) a_s[l * F32_ASTRIDE + lane] = ga[lane + l * m];
+                } else {
+                    if (lane < kk)
+                        for (int i = 0; i < m; i++) a_s[lane * F32_ASTRIDE + i] = ga[lane + i * kk];
+                }
+                // op(B) is kk x n: element (l, j) at l + j*kk (TB = 0) or j + l*n (TB = 1)
+                if (!TB) {
+                    if (lane < kk)
+                        for (int j = 0; j < n; j++) b_s[j * F32_BSTRIDE + lane] = gb[lane + j * kk];
+                } else {
+                    if (lane < n)
+                        for (int l = 0; l < kk; l++) b_s[lane * F32_BSTRIDE + l] = gb[lane + l * n];
+                }
+                __syncwarp();
+                if (lane < n) {
+                    for (int l = 0; l < kk; l++) {
+                        const float b = b_s[lane * F32_BSTRIDE + l];
+                        const float4* ac = reinterpret_cast<const float4*>(a_s + l * F32_ASTRIDE);
+#pragma unroll
+                        for (int i4 = 0; i4 < 8; i4++) {
+                            if (4 * i4 < m) {
+                                const float4 av = ac[i4];
+                                acc[4 * i4 + 0] = fmaf(av.x, b, acc[4 * i4 + 0]);
+                                acc[4 * i4 + 1] = fmaf(av.y, b, acc[4 * i4 + 1]);
+                                acc[4 * i4 + 2] = fmaf(av.z, b, acc[4 * i4 + 2]);
+                                acc[4 * i4 + 3] = fmaf(av.w, b, acc[4 * i4 + 3]);
+                            }
+                        }
+                    }
+                }
+            }
+            // column j = lane of the C block; alpha / beta in FP64
+            if (lane < n) {
+                double* cout = g.Cd + g.c_off[cb] + (int64_t)lane * m;
+                const int o = g.c_old ? g.c_old[cb] : -1;
+                const double* cold = o >= 0 ? g.Cold + g.Cold_off[o] + (int64_t)lane * m : nullptr;
+#pragma unroll
+                for (int i = 0; i < 32; i++) {
+                    if (i < m) {
+                        double v = __dmul_rn(g.alpha, (double)acc[i]);
+                        if (cold) v = __dadd_rn(v, __dmul_rn(g.beta, cold[i]));
+                        cout[i] = v;
+                    }
+                }
+            }
+        }
+    }
+}
+
 // FP64 -> FP32, round to nearest even
 __global__ void k_to_f32(int64_t n, const double* __restrict__ in, float* __restrict__ out) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -382,9 +477,30 @@ int to_f32(const double* in, int64_t n, float* out) {
     return DBCSR_OK;
 }
 
-// FP32 stack kernels: C blocks grouped by elements-per-lane class, one warp each.
-int smm_fp32_dispatch(const SmmArgs& g, int max_mn) {
+// FP32 stack kernels: blocks up to 32 x 32 on the shared-memory kernel (one
+// launch), larger ones grouped by elements-per-lane class, one warp each.
+int smm_fp32_dispatch(const SmmArgs& g, int max_mn, int max_edge) {
     if (g.nC == 0) return DBCSR_OK;
+    if (max_edge <= 32) {
+        cudaStream_t st = ctx().stream;
+        int grid = ctx().num_sms * 3;
+        if ((int64_t)grid * F32_WARPS > g.nC) grid = (int)cdiv(g.nC, F32_WARPS);
+        const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(16, g.nC / ((int64_t)grid * F32_WARPS * 4)));
+        const int ta = g.A.trans, tb = g.B.trans;
+#define DB_LAUNCH_F32(TA_, TB_)                                                                          \
+    do {                                                                                                \
+        DB_CUDA(cudaFuncSetAttribute(k_smm_f32_tile<TA_, TB_>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                     F32_SMEM));                                                        \
+        k_smm_f32_tile<TA_, TB_><<<grid, 32 * F32_WARPS, F32_SMEM, st>>>(g, chunk);                     \
+    } while (0)
+        if (!ta && !tb) DB_LAUNCH_F32(0, 0);
+        else if (ta && !tb) DB_LAUNCH_F32(1, 0);
+        else if (!ta && tb) DB_LAUNCH_F32(0, 1);
+        else DB_LAUNCH_F32(1, 1);
+#undef DB_LAUNCH_F32
+        DB_KCHECK();
+        return DBCSR_OK;
+    }
     if (g.nC >= INT32_MAX) return fail(DBCSR_ERR_OVERFLOW, "stack kernels: too many C blocks");
     cudaStream_t st = ctx().stream;
     DBuf<uint32_t> key, idx;
