@@ -393,6 +393,8 @@ def main():
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
         hA, hB = pin(w.A.data), pin(w.B.data)
         hC = pin(C0.data) if C0 is not None else None
+        # the result is read into pinned host memory too (allocated once, like the inputs)
+        hOut = pin(np.zeros(max(1, int(Cm.info()[3])), np.float64))
         out = None
 
         def e2e_step():
@@ -404,8 +406,9 @@ def main():
             else:
                 Ch = dbcsr.Matrix.create(rs, cs, np.zeros(0, np.int32), np.zeros(0, np.int32))
             dbcsr.multiply(w.transa, w.transb, w.alpha, Ah, Bh, w.beta, Ch, path=args.path, precision=precision,
-                           ozaki_slices=args.slices, kernel=args.kernel)
-            out = Ch.data()
+                           ozaki_slices=args.slices, kernel=args.kernel, hybrid_panel=hpanel,
+                           hybrid_fill_pct=args.hybrid_fill)
+            out = Ch.data(hOut)
             for m in (Ah, Bh, Ch):
                 m.release()
 

@@ -208,9 +208,14 @@ class Matrix:
         _check(load().dbcsr_get_index(self._h, _ip(br), _ip(bc), off.ctypes.data_as(_LP)))
         return br[:n], bc[:n], off[:n]
 
-    def data(self) -> np.ndarray:
+    def data(self, out: np.ndarray | None = None) -> np.ndarray:
+        """The stored values (CSR block order) on the host; ``out``: a float64
+        host array of at least nelems entries to fill (e.g. pinned memory)."""
         nbr, nbc, n, e = self.info()
-        out = np.zeros(max(e, 1), np.float64)
+        if out is None:
+            out = np.zeros(max(e, 1), np.float64)
+        elif out.dtype != np.float64 or out.size < e or not out.flags["C_CONTIGUOUS"]:
+            raise ValueError("out: contiguous float64 array with at least nelems entries")
         _check(load().dbcsr_get_data(self._h, out.ctypes.data_as(C.c_void_p), 0))
         return out[:e]
 
