@@ -48,6 +48,32 @@ def peaks():
         return dict(FALLBACK), "fallback"
 
 
+TRAFFIC_TABLE = os.path.join(ROOT, "profiles", "dram_traffic.md")
+
+
+def dram_traffic(workload_name, precision, path):
+    """DRAM bytes (read + write) per launch of the dominant kernel, from the ncu
+    capture recorded in profiles/dram_traffic.md; None unless the kernel's
+    source file is unchanged since (its SHA-256 is recorded with the number)."""
+    import hashlib
+    try:
+        lines = open(TRAFFIC_TABLE).read().splitlines()
+    except OSError:
+        return None
+    for ln in lines:
+        cells = [c.strip() for c in ln.strip().strip("|").split("|")]
+        if len(cells) != 7 or cells[0] != workload_name or cells[1] != precision or cells[2] != path:
+            continue
+        try:
+            with open(os.path.join(ROOT, cells[4]), "rb") as f:
+                if hashlib.sha256(f.read()).hexdigest() != cells[5]:
+                    return None
+            return float(cells[6])
+        except (OSError, ValueError):
+            return None
+    return None
+
+
 def workload(name, scale, occ=0.1):
     from paper_1910_04796_gb300 import synth
     if name == "dense-limit":
@@ -347,8 +373,8 @@ def main():
         peak_note = f"TF32 = {pk_kind} bf16 burst x nominal TF32/bf16 (1100/2250)"
         achieved = s2["main_flops"] / (main_ms / 1e3) / 1e12
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
-                "traffic": None, "kernel_ms": main_ms, "algorithmic_flops": s2["main_flops"],
-                "peak_source": peak_note}
+                "traffic": dram_traffic(w.name, precision, path_taken), "kernel_ms": main_ms,
+                "algorithmic_flops": s2["main_flops"], "peak_source": peak_note}
 
     # comparison legs on the same GPU and inputs: the plain FP64 paths, the
     # emulated and TF32 paths with their error against the GPU FP64 result
