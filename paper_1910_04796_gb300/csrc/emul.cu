@@ -179,10 +179,17 @@ __device__ __forceinline__ double scale2(double acc, int k) {
 // stride ldws) into column-major C, through a 32 x 32 shared-memory tile so
 // that both the reads and the writes are coalesced. Same arithmetic and order
 // as k_recombine.
-__global__ void __launch_bounds__(256) k_recombine_rm(int64_t M, int64_t N, int s, int ksegs, const int* __restrict__ ws,
+// S (the slice count) is a template parameter: the level weights become
+// constant shifts. The levels are joined as U 2^(7 (S - NU)) + V, U over the
+// first NU = min(4, S) levels and V over the rest, each an int64 Horner sum
+// (|U|, |V| < 2^64 while every level sum stays below 2^40, i.e. fewer than
+// 2^9 K segments of 16 384), then one 128-bit step and one rounding.
+template <int S>
+__global__ void __launch_bounds__(256) k_recombine_rm(int64_t M, int64_t N, int ksegs, const int* __restrict__ ws,
                                                       int64_t ldws, const int* __restrict__ e,
                                                       const int* __restrict__ f, double alpha, double beta,
                                                       double* __restrict__ C, int64_t ldc) {
+    constexpr int NU = S < 4 ? S : 4;
     __shared__ double tile[32][33];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
     const int64_t i0 = (int64_t)blockIdx.y * 32, j0 = (int64_t)blockIdx.x * 32;
@@ -191,13 +198,16 @@ __global__ void __launch_bounds__(256) k_recombine_rm(int64_t M, int64_t N, int 
         const int64_t i = i0 + r, j = j0 + tx;
         double acc = 0.0;
         if (i < M && j < N) {
-            __int128 S = 0;   // exact sum of the level sums, each shifted to its weight
-            for (int d = 2; d <= s + 1; d++) {
-                int64_t g = 0;   // exact: sum over K segments of int32 partial sums
-                for (int k = 0; k < ksegs; k++) g += ws[((int64_t)(d - 2) * ksegs + k) * lstride + i * ldws + j];
-                S += (__int128)g << (7 * (s + 1 - d));
+            long long U = 0, V = 0;
+#pragma unroll
+            for (int d = 0; d < S; d++) {
+                long long g = 0;   // exact: sum over K segments of int32 partial sums
+                for (int k = 0; k < ksegs; k++) g += ws[((int64_t)d * ksegs + k) * lstride + i * ldws + j];
+                if (d < NU) U = U * 128 + g;
+                else V = V * 128 + g;
             }
-            acc = emul::round_i128_scaled(S, e[i] + f[j] - 7 * (s + 1));
+            const __int128 Sx = (__int128)U * ((__int128)1 << (7 * (S - NU))) + V;
+            acc = emul::round_i128_scaled(Sx, e[i] + f[j] - 7 * (S + 1));
         }
         tile[r][tx] = acc;
     }
@@ -315,7 +325,13 @@ int dgemm_ozaki(int64_t M, int64_t N, int64_t K, double alpha, const double* A, 
         DB_CUDA(cudaMemcpyAsync(&h_err, p.err, sizeof(int), cudaMemcpyDeviceToHost, st));
         dim3 g((unsigned)cdiv(N, 32), (unsigned)cdiv(M, 32));
         if (g.y > 65535) return fail(DBCSR_ERR_OVERFLOW, "emulated gemm: M too large for the recombination grid");
-        k_recombine_rm<<<g, 256, 0, st>>>(M, N, s, p.ksegs, wsi.p, p.ldws, e.p, f.p, alpha, beta, C, ldc);
+        if (p.ksegs >= 512) return fail(DBCSR_ERR_OVERFLOW, "emulated gemm: K too large for exact level sums");
+        switch (s) {
+#define DB_RC(S_) case S_: k_recombine_rm<S_><<<g, 256, 0, st>>>(M, N, p.ksegs, wsi.p, p.ldws, e.p, f.p, alpha, beta, C, ldc); break
+            DB_RC(1); DB_RC(2); DB_RC(3); DB_RC(4); DB_RC(5); DB_RC(6); DB_RC(7);
+            default: DB_RC(8);
+#undef DB_RC
+        }
         DB_KCHECK();
     } else {
         DBuf<double> ws;
