@@ -565,10 +565,9 @@ bool plan_matches(const ReusePlan* rp, bool ta, bool tb, double alpha, double be
            rp->alpha == alpha && rp->beta == beta && rp->use_old == (beta != 0.0);
 }
 
-// The product kernels over C blocks [b0, b1) of the plan (one contiguous run
-// of C block rows): the same arguments with the C-block arrays offset.
-int stack_run(const SmmArgs& g0, int64_t b0, int64_t b1, int64_t nprod, dbcsr_matrix_s* A, bool ta,
-              dbcsr_matrix_s* B, bool tb, dbcsr_matrix_s* C, const dbcsr_opts& o, double* flops) {
+// The FP64 product kernels over C blocks [b0, b1) of the plan (one contiguous
+// run of C block rows): the same arguments with the C-block arrays offset.
+int fp64_stack_run(const SmmArgs& g0, int64_t b0, int64_t b1, dbcsr_matrix_s* C, const dbcsr_opts& o) {
     if (b1 <= b0) return DBCSR_OK;
     SmmArgs g = g0;
     g.nC = b1 - b0;
@@ -578,11 +577,7 @@ int stack_run(const SmmArgs& g0, int64_t b0, int64_t b1, int64_t nprod, dbcsr_ma
     if (g.c_old) g.c_old += b0;
     g.c_pstart += b0;
     DB_CUDA(cudaMemsetAsync(g.counter, 0, sizeof(unsigned long long), g_ctx.stream));
-    if (o.precision == DBCSR_PREC_FP64) return smm_fp64_dispatch(g, C->max_rs * C->max_cs, o.kernel);
-    double f = 0.0;
-    DB_TRY(smm_emulated(g, A, ta, B, tb, C, o, nprod, &f));
-    *flops += f;
-    return DBCSR_OK;
+    return smm_fp64_dispatch(g, C->max_rs * C->max_cs, o.kernel);
 }
 
 // Hybrid partial densification: Sec. III coalesces all blocks of a dense
@@ -654,7 +649,7 @@ int hybrid_products(const SmmArgs& g, const StackPlan& P, double* data, bool ta,
         const int64_t b0 = crp[r0], b1 = crp[r1];
         if (!dense_run[q]) {
             if (o.precision == DBCSR_PREC_FP64) {
-                DB_TRY(stack_run(g, b0, b1, ps[b1] - ps[b0], A, ta, B, tb, C, o, &flops));
+                DB_TRY(fp64_stack_run(g, b0, b1, C, o));
             } else {
                 sparse.push_back({b0, b1});   // emulated: one call, operands sliced once
                 sparse_prod += ps[b1] - ps[b0];
@@ -889,6 +884,26 @@ __global__ void k_full_index(int nbr, int nbc, const int* __restrict__ rs, const
     if (b == 0) off[nb] = roff[nbr] * N;
 }
 
+// Give C the fully occupied index (every block, CSR order) with fresh data.
+int install_full_index(dbcsr_matrix_s* C, int64_t M, int64_t N) {
+    const int64_t nb = (int64_t)C->nbr * C->nbc;
+    if (nb >= INT32_MAX) return fail(DBCSR_ERR_OVERFLOW, "multiply: result has too many blocks");
+    int *rowptr = nullptr, *col = nullptr, *row_of = nullptr;
+    int64_t* off = nullptr;
+    double* data = nullptr;
+    DB_TRY(dalloc(&rowptr, (size_t)C->nbr + 1));
+    DB_TRY(dalloc(&col, (size_t)nb));
+    DB_TRY(dalloc(&row_of, (size_t)nb));
+    DB_TRY(dalloc(&off, (size_t)nb + 1));
+    DB_TRY(dalloc(&data, (size_t)(M * N)));
+    int64_t cnt = std::max<int64_t>(nb, C->nbr + 1);
+    k_full_index<<<(unsigned)cdiv(cnt, 256), 256, 0, g_ctx.stream>>>(C->nbr, C->nbc, C->d_rs, C->d_cs, C->d_roff,
+                                                                     C->d_coff, N, rowptr, col, row_of, off);
+    DB_KCHECK();
+    install(C, nb, M * N, rowptr, col, row_of, off, data);
+    return DBCSR_OK;
+}
+
 int multiply_dense(bool ta, bool tb, double alpha, dbcsr_matrix_s* A, dbcsr_matrix_s* B, double beta,
                    dbcsr_matrix_s* C, const dbcsr_opts& o) {
     const int64_t M = C->h_roff[C->nbr], N = C->h_coff[C->nbc];
@@ -897,6 +912,24 @@ int multiply_dense(bool ta, bool tb, double alpha, dbcsr_matrix_s* A, dbcsr_matr
     const bool b_full = B->nblks == (int64_t)B->nbr * B->nbc;
     const bool use_old = beta != 0.0 && C->nblks > 0;
     const int nbk = ta ? A->nbr : A->nbc;
+    const bool c_full = C->nblks == (int64_t)C->nbr * C->nbc && C->nblks > 0;
+    // Emulated FP64 with fully occupied operands: slices cut straight from the
+    // blocks and the result recombined straight into C's blocks (no dense
+    // copies of A, B, C). C is (made) fully occupied; its old values are used
+    // in place when beta != 0.
+    if (o.precision == DBCSR_PREC_OZAKI && a_full && b_full && nbk > 0 && M > 0 && N > 0 && K > 0 &&
+        (!use_old || c_full) && ozaki_blocks_ok(N)) {
+        const int s = o.ozaki_slices > 0 ? o.ozaki_slices : 7;
+        if (s > 8) return fail(DBCSR_ERR_ARG, "ozaki_slices must be 1..8");
+        mark(0);
+        if (!c_full) DB_TRY(install_full_index(C, M, N));
+        mark(1);
+        DB_TRY(dgemm_ozaki_blocks(A, ta, B, tb, C, alpha, use_old ? beta : 0.0, s, &g_stats.main_flops));
+        mark(2);
+        mark(3);
+        g_stats.c_blocks = C->nblks;
+        return DBCSR_OK;
+    }
     // result pattern: full when both operands are full (and K > 0); else the
     // symbolic product (through stack generation's pattern pass)
     DBuf<double> dA, dB, dC;
@@ -921,23 +954,7 @@ int multiply_dense(bool ta, bool tb, double alpha, dbcsr_matrix_s* A, dbcsr_matr
     // new C index
     if (a_full && b_full && nbk > 0) {
         const bool same = C->nblks == (int64_t)C->nbr * C->nbc;   // old C already full, CSR-ordered
-        if (!same) {
-            const int64_t nb = (int64_t)C->nbr * C->nbc;
-            if (nb >= INT32_MAX) return fail(DBCSR_ERR_OVERFLOW, "multiply: result has too many blocks");
-            int *rowptr = nullptr, *col = nullptr, *row_of = nullptr;
-            int64_t* off = nullptr;
-            double* data = nullptr;
-            DB_TRY(dalloc(&rowptr, (size_t)C->nbr + 1));
-            DB_TRY(dalloc(&col, (size_t)nb));
-            DB_TRY(dalloc(&row_of, (size_t)nb));
-            DB_TRY(dalloc(&off, (size_t)nb + 1));
-            DB_TRY(dalloc(&data, (size_t)(M * N)));
-            int64_t cnt = std::max<int64_t>(nb, C->nbr + 1);
-            k_full_index<<<(unsigned)cdiv(cnt, 256), 256, 0, g_ctx.stream>>>(
-                C->nbr, C->nbc, C->d_rs, C->d_cs, C->d_roff, C->d_coff, N, rowptr, col, row_of, off);
-            DB_KCHECK();
-            install(C, nb, M * N, rowptr, col, row_of, off, data);
-        }
+        if (!same) DB_TRY(install_full_index(C, M, N));
         DB_TRY(undensify(C, dC.p, M));
         mark(3);
         g_stats.c_blocks = C->nblks;

@@ -18,6 +18,7 @@
 
 #include "emul.cuh"
 #include "emul_common.cuh"
+#include "smm_emul.cuh"
 #include "tc_gemm.cuh"
 
 namespace dbcsr {
@@ -184,11 +185,26 @@ __device__ __forceinline__ double scale2(double acc, int k) {
 // first NU = min(4, S) levels and V over the rest, each an int64 Horner sum
 // (|U|, |V| < 2^64 while every level sum stays below 2^40, i.e. fewer than
 // 2^9 K segments of 16 384), then one 128-bit step and one rounding.
+// Output of the recombination: a column-major C (ldc), or, with `base`, the
+// storage of a fully occupied block matrix (blocks in CSR order, each
+// column-major), where element (i, j) lives at C[base[i] + stride[i] * j]
+// (base[i] = roff(i's block row) * N + i's row within the block, stride[i] =
+// that block row's size). Old values are read from the same place.
+struct OzOut {
+    double* C;
+    int64_t ldc;
+    const int64_t* base;
+    const int* stride;
+    __device__ __forceinline__ int64_t at(int64_t i, int64_t j) const {
+        return base ? base[i] + (int64_t)stride[i] * j : i + j * ldc;
+    }
+};
+
 template <int S>
 __global__ void __launch_bounds__(256) k_recombine_rm(int64_t M, int64_t N, int ksegs, const int* __restrict__ ws,
                                                       int64_t ldws, const int* __restrict__ e,
                                                       const int* __restrict__ f, double alpha, double beta,
-                                                      double* __restrict__ C, int64_t ldc) {
+                                                      OzOut out) {
     constexpr int NU = S < 4 ? S : 4;
     __shared__ double tile[32][33];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
@@ -215,9 +231,63 @@ __global__ void __launch_bounds__(256) k_recombine_rm(int64_t M, int64_t N, int 
     for (int cc = ty; cc < 32; cc += 8) {
         const int64_t i = i0 + tx, j = j0 + cc;
         if (i < M && j < N) {
+            const int64_t a = out.at(i, j);
             double v = __dmul_rn(alpha, tile[tx][cc]);
-            if (beta != 0.0) v = __dadd_rn(v, __dmul_rn(beta, C[i + j * ldc]));
-            C[i + j * ldc] = v;
+            if (beta != 0.0) v = __dadd_rn(v, __dmul_rn(beta, out.C[a]));
+            out.C[a] = v;
+        }
+    }
+}
+
+// element-row layout of a fully occupied block matrix (see OzOut)
+__global__ void k_full_rows(int nbr, const int* __restrict__ rs, const int64_t* __restrict__ roff, int64_t N,
+                            int64_t* __restrict__ base, int* __restrict__ stride) {
+    const int bi = blockIdx.x;
+    if (bi >= nbr) return;
+    const int m = rs[bi];
+    const int64_t r0 = roff[bi];
+    for (int r = threadIdx.x; r < m; r += blockDim.x) {
+        base[r0 + r] = r0 * N + r;
+        stride[r0 + r] = m;
+    }
+}
+
+// Slices of every stored block of one operand, written straight into the
+// dense K-major slice layout S[(t-1) * rows + x][l] (row stride ldk): x is
+// the op() line (row of op(A) / column of op(B)), l the inner index. A warp
+// per block, lanes along l; a block (at most a few KB) stays in L1 while its
+// lines are read, so the strided reads cost little. Two consecutive l per
+// lane (4-byte stores) when the block's first l and its width are even.
+__global__ void k_slice_blocks(SliceGeom G, const int* __restrict__ ex, int s, int64_t rows, int64_t ldk,
+                               __nv_bfloat16* __restrict__ S) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t plane = rows * ldk;
+    for (int64_t b = w0; b < G.nblks; b += nw) {
+        int X, L, xs, ls;
+        int64_t xbase;
+        geom_block(G, b, X, L, xs, ls, xbase);
+        const int64_t lbase = G.x_is_row ? G.coff[G.col[b]] : G.roff[G.row_of[b]];
+        const double* d = G.data + G.off[b];
+        const bool pairs = ((lbase | L | ldk) & 1) == 0;
+        for (int x = 0; x < X; x++) {
+            const int e = ex[xbase + x];
+            __nv_bfloat16* o = S + (xbase + x) * ldk + lbase;
+            if (pairs) {
+                for (int l = 2 * lane; l < L; l += 64) {
+                    const long long q0 = fixed_point(d[(int64_t)x * xs + (int64_t)l * ls], e, s);
+                    const long long q1 = fixed_point(d[(int64_t)x * xs + (int64_t)(l + 1) * ls], e, s);
+                    for (int t = 1; t <= s; t++)
+                        *reinterpret_cast<__nv_bfloat162*>(o + (int64_t)(t - 1) * plane + l) =
+                            __halves2bfloat162(slice_bf16(q0, t, s), slice_bf16(q1, t, s));
+                }
+            } else {
+                for (int l = lane; l < L; l += 32) {
+                    const long long q = fixed_point(d[(int64_t)x * xs + (int64_t)l * ls], e, s);
+                    for (int t = 1; t <= s; t++) o[(int64_t)(t - 1) * plane + l] = slice_bf16(q, t, s);
+                }
+            }
         }
     }
 }
@@ -260,6 +330,11 @@ int oz_exponents(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda, 
     return DBCSR_OK;
 }
 
+// the slice GEMMs and the recombination into `out` (steps 3 and 4)
+int oz_run(int64_t M, int64_t N, int64_t K, int64_t ldk, int s, const __nv_bfloat16* SA_p,
+           const __nv_bfloat16* SB_p, const int* e_p, const int* f_p, double alpha, double beta, const OzOut& out,
+           double* main_flops);
+
 int dgemm_ozaki(int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda, const double* B,
                 int64_t ldb, double beta, double* C, int64_t ldc, int s, double* main_flops, double* main_ms_unused) {
     (void)main_ms_unused;
@@ -289,6 +364,17 @@ int dgemm_ozaki(int64_t M, int64_t N, int64_t K, double alpha, const double* A, 
         k_slice_cols<<<g2, 256, 0, st>>>(N, K, ldk, B, ldb, f.p, s, SB.p);
         DB_KCHECK();
     }
+    return oz_run(M, N, K, ldk, s, SA.p, SB.p, e.p, f.p, alpha, beta, OzOut{C, ldc, nullptr, nullptr}, main_flops);
+}
+
+int oz_run(int64_t M, int64_t N, int64_t K, int64_t ldk, int s, const __nv_bfloat16* SA_p,
+           const __nv_bfloat16* SB_p, const int* e_p, const int* f_p, double alpha, double beta, const OzOut& out,
+           double* main_flops) {
+    cudaStream_t st = ctx().stream;
+    struct { const __nv_bfloat16* p; } SA{SA_p}, SB{SB_p};
+    struct { const int* p; } e{e_p}, f{f_p};
+    double* C = out.C;
+    const int64_t ldc = out.ldc;
     // 128 x 256 tiles when the output is wide enough (fewer bytes moved per
     // flop), else 128 x 128 tiles in clusters of two sharing the B tile
     const bool wide = N >= 256 && tc256_usable();
@@ -327,13 +413,14 @@ int dgemm_ozaki(int64_t M, int64_t N, int64_t K, double alpha, const double* A, 
         if (g.y > 65535) return fail(DBCSR_ERR_OVERFLOW, "emulated gemm: M too large for the recombination grid");
         if (p.ksegs >= 512) return fail(DBCSR_ERR_OVERFLOW, "emulated gemm: K too large for exact level sums");
         switch (s) {
-#define DB_RC(S_) case S_: k_recombine_rm<S_><<<g, 256, 0, st>>>(M, N, p.ksegs, wsi.p, p.ldws, e.p, f.p, alpha, beta, C, ldc); break
+#define DB_RC(S_) case S_: k_recombine_rm<S_><<<g, 256, 0, st>>>(M, N, p.ksegs, wsi.p, p.ldws, e.p, f.p, alpha, beta, out); break
             DB_RC(1); DB_RC(2); DB_RC(3); DB_RC(4); DB_RC(5); DB_RC(6); DB_RC(7);
             default: DB_RC(8);
 #undef DB_RC
         }
         DB_KCHECK();
     } else {
+        if (out.base) return fail(DBCSR_ERR_STATE, "emulated gemm: block-layout output needs the 256-wide kernel");
         DBuf<double> ws;
         DB_TRY(ws.alloc((size_t)s * p.ksegs * M * N));
         p.ws = ws.p;
@@ -350,6 +437,45 @@ int dgemm_ozaki(int64_t M, int64_t N, int64_t K, double alpha, const double* A, 
     // algorithmic slice-GEMM flops: one M x N x K product per slice pair (unpadded)
     if (main_flops) *main_flops = 2.0 * (double)M * (double)N * (double)K * (double)(s * (s + 1) / 2);
     return DBCSR_OK;
+}
+
+bool ozaki_blocks_ok(int64_t N) { return N >= 256 && tc256_usable(); }
+
+int dgemm_ozaki_blocks(dbcsr_matrix_s* A, bool ta, dbcsr_matrix_s* B, bool tb, dbcsr_matrix_s* C, double alpha,
+                       double beta, int s, double* main_flops) {
+    cudaStream_t st = ctx().stream;
+    const int64_t M = C->h_roff[C->nbr], N = C->h_coff[C->nbc];
+    const int64_t K = ta ? A->h_roff[A->nbr] : A->h_coff[A->nbc];
+    if (M == 0 || N == 0 || K == 0) return fail(DBCSR_ERR_STATE, "emulated block gemm: empty operand");
+    if (M >= INT32_MAX || N >= INT32_MAX) return fail(DBCSR_ERR_OVERFLOW, "emulated gemm: dimension too large");
+    const int64_t ldk = cdiv(K, 64) * 64;
+    DBuf<int> e, f;
+    DB_TRY(line_exponents(A, !ta, M, e));
+    DB_TRY(line_exponents(B, tb, N, f));
+    DBuf<__nv_bfloat16> SA, SB;
+    DB_TRY(SA.alloc((size_t)s * M * ldk));
+    DB_TRY(SB.alloc((size_t)s * N * ldk));
+    if (ldk > K) {   // the K padding of every slice row reads as zero
+        DB_CUDA(cudaMemset2DAsync(SA.p + K, ldk * sizeof(__nv_bfloat16), 0, (ldk - K) * sizeof(__nv_bfloat16),
+                                  (size_t)s * M, st));
+        DB_CUDA(cudaMemset2DAsync(SB.p + K, ldk * sizeof(__nv_bfloat16), 0, (ldk - K) * sizeof(__nv_bfloat16),
+                                  (size_t)s * N, st));
+    }
+    const int sgrid = ctx().num_sms * 16;
+    k_slice_blocks<<<(int)std::min<int64_t>(cdiv(A->nblks, 8), sgrid), 256, 0, st>>>(slice_geom(A, !ta), e.p, s,
+                                                                                     M, ldk, SA.p);
+    DB_KCHECK();
+    k_slice_blocks<<<(int)std::min<int64_t>(cdiv(B->nblks, 8), sgrid), 256, 0, st>>>(slice_geom(B, tb), f.p, s, N,
+                                                                                     ldk, SB.p);
+    DB_KCHECK();
+    DBuf<int64_t> base;
+    DBuf<int> stride;
+    DB_TRY(base.alloc(M));
+    DB_TRY(stride.alloc(M));
+    k_full_rows<<<C->nbr, 128, 0, st>>>(C->nbr, C->d_rs, C->d_roff, N, base.p, stride.p);
+    DB_KCHECK();
+    return oz_run(M, N, K, ldk, s, SA.p, SB.p, e.p, f.p, alpha, beta, OzOut{C->d_data, 0, base.p, stride.p},
+                  main_flops);
 }
 
 int dgemm_emulated(int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda, const double* B,

@@ -342,6 +342,9 @@ int slices_of(dbcsr_matrix_s* M, bool x_is_row, const int* ex, int s, DBuf<int64
     return DBCSR_OK;
 }
 
+
+}  // namespace
+
 int line_exponents(dbcsr_matrix_s* M, bool x_is_row, int64_t nlines, DBuf<int>& ex) {
     cudaStream_t st = ctx().stream;
     const SliceGeom G = slice_geom(M, x_is_row);
@@ -360,8 +363,6 @@ int line_exponents(dbcsr_matrix_s* M, bool x_is_row, int64_t nlines, DBuf<int>& 
     }
     return DBCSR_OK;
 }
-
-}  // namespace
 
 int smm_emulated(const SmmArgs& g, dbcsr_matrix_s* A, bool ta, dbcsr_matrix_s* B, bool tb, dbcsr_matrix_s* C,
                  const dbcsr_opts& o, int64_t nprod, double* main_flops, const CRanges* ranges) {

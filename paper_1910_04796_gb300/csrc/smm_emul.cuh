@@ -38,6 +38,11 @@ inline SliceGeom slice_geom(dbcsr_matrix_s* M, bool x_is_row) {
                      M->nblks, x_is_row ? 1 : 0};
 }
 
+// frexp exponents of the maximum |x| of each op() line of M (element rows of
+// op(A) when x_is_row describes op(A)'s rows, element columns of op(B)), from
+// the stored blocks; nlines entries
+int line_exponents(dbcsr_matrix_s* M, bool x_is_row, int64_t nlines, DBuf<int>& ex);
+
 // tcgen05 variant (smm_emul_tc.cu): every block padded to 32 x 32; e, f are the
 // exponents of op(A)'s element rows and op(B)'s element columns. issued_flops
 // receives the tensor-core arithmetic issued (padded operand shapes).

@@ -25,8 +25,9 @@
 //       epilogue's work over the quadrants
 // so pair (t, u) owns a 32 x 32 accumulator block of TMEM (lane quadrant
 // t - 1 or s - t, columns 32 (u-1), + 32 s for G2); pairs with t + u > s + 1
-// are computed and ignored. An fp32 accumulator is exact for 32 products
-// (32 * 32 * 127^2 < 2^24): a C block's products run in chunks of 32.
+// are computed and ignored. A C block's products run in chunks of 16: an fp32
+// accumulator then stays below 2^23 (16 * 32 * 127^2), so the G1 and G2 sums
+// of a level are added exactly in fp32 before one conversion to int32.
 //
 // Warps: 0 bulk-copy producer (one lane), 1 TMEM owner and MMA issuer (one
 // lane), 2-9 epilogue; epilogue warp w reads TMEM lane quadrant q = w % 4,
@@ -63,7 +64,7 @@ constexpr int TC_EL = 8 / TC_R;               // C elements per epilogue thread
 constexpr int TC_SLOT = 2048;                 // one 32 x 32 bf16 slice
 constexpr int TC_SMEM_CAP = 232448;           // 227 KB of shared memory per CTA
 constexpr int TC_SMEM_MIN = 120 * 1024;       // one CTA per SM: it allocates all 512 TMEM columns
-constexpr int TC_CHUNK = 32;                  // products per exact fp32 stretch
+constexpr int TC_CHUNK = 16;                  // products per exact fp32 stretch (16 * 32 * 127^2 < 2^23)
 constexpr uint64_t TC_WAIT_NS = 4000000000ull;
 // C blocks are visited tile by tile: the CTAs working at the same time share
 // the tile's A block rows and B block columns, which stay in L2
@@ -390,10 +391,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_smm_emul_tc(TcArgs a) {
                             int v0[4], v1[4];
 #pragma unroll
                             for (int k = 0; k < 4; k++) {
-                                v0[k] = __float2int_rn(__uint_as_float(ra[c * 4 + k]));
-                                if (g0) v0[k] += __float2int_rn(__uint_as_float(rc[c * 4 + k]));
-                                v1[k] = __float2int_rn(__uint_as_float(rb[c * 4 + k]));
-                                if (g1) v1[k] += __float2int_rn(__uint_as_float(rd[c * 4 + k]));
+                                // both pair sums are integers below 2^23: their fp32 sum is exact
+                                float x0 = __uint_as_float(ra[c * 4 + k]);
+                                if (g0) x0 += __uint_as_float(rc[c * 4 + k]);
+                                float x1 = __uint_as_float(rb[c * 4 + k]);
+                                if (g1) x1 += __uint_as_float(rd[c * 4 + k]);
+                                v0[k] = __float2int_rn(x0);
+                                v1[k] = __float2int_rn(x1);
                             }
                             const int off = ((r * (TC_COLS / 4) + c) ^ sw) << 4;
                             *reinterpret_cast<int4*>(row0 + off) = make_int4(v0[0], v0[1], v0[2], v0[3]);
