@@ -303,7 +303,7 @@ def version() -> str:
 
 
 def has_precision(name: str) -> bool:
-    """Whether this build implements the given precision (fp64, ozaki, tf32)."""
+    """Whether the library implements the given precision (fp64, ozaki, tf32, fp32)."""
     return name in _AVAILABLE
 
 
