@@ -68,3 +68,13 @@ def test_fp32_dense_path_rejected():
     # automatic path choice keeps FP32 on the stacks even for full operands
     got, st = gpu_multiply("N", "N", 1.0, A, B, 0.0, path="auto", precision="fp32")
     assert st["path"] == dbcsr.PATH_STACKS
+
+
+def test_fp32_blocks_larger_than_32_use_the_generic_kernel():
+    rng = np.random.default_rng(903)
+    A, B, Cm = synth.random_small(rng, 4, 5, 3, p=0.7, sizes=(20, 40, 48), with_c=True, c_p=0.5)
+    got, _ = gpu_multiply("N", "T", 1.0, A, synth.transpose_blocks(B), 0.5, Cm, path="stacks", precision="fp32")
+    ref = O.multiply("N", "N", 1.0, A, B, 0.5, Cm, mode=2)
+    assert_same_pattern(got, ref)
+    K = int(np.sum(A.col_sizes))
+    assert normwise(got, ref, A, B) <= 2 * _gamma(K) + 1e-15

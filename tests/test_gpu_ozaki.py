@@ -102,3 +102,39 @@ def test_ozaki_error_decreases_with_slices():
         got, _ = gpu_multiply("N", "N", 1.0, A, B, 0.0, path="dense", precision="ozaki", ozaki_slices=s)
         errs.append(O.normwise_error(O.densify(got), O.densify(ref), O.densify(A), O.densify(B)))
     assert all(errs[q + 1] <= errs[q] * 1.0001 + 1e-17 for q in range(len(errs) - 1))
+
+
+@pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("N", "T"), ("T", "T")])
+def test_fused_block_path_transposes_beta(ta, tb):
+    # fully occupied operands with N >= 256: slices are cut straight from the
+    # blocks and the result is recombined into C's blocks in place (beta != 0)
+    rng = np.random.default_rng(470)
+    A = synth.dense_matrix(rng, 6, 7, 22, 22)
+    B = synth.dense_matrix(rng, 7, 13, 22, 22)      # N = 286
+    Cm = synth.dense_matrix(rng, 6, 13, 22, 22)
+    As = synth.transpose_blocks(A) if ta == "T" else A
+    Bs = synth.transpose_blocks(B) if tb == "T" else B
+    got, _ = gpu_multiply(ta, tb, -0.5, As, Bs, 2.0, Cm, path="dense", precision="ozaki")
+    ref, _, _ = ozaki_ref(A, B, Cm, -0.5, 2.0, 7)
+    assert_same_pattern(got, ref)
+    assert np.array_equal(got.data, ref.data)
+
+
+def test_fused_block_path_uneven_sizes_partial_old_c():
+    # uneven block sizes (odd offsets: single bf16 stores); an old C that is not
+    # fully occupied with beta != 0 takes the densifying path instead
+    rng = np.random.default_rng(471)
+    rs = np.array([5, 13, 23, 26, 32, 7], np.int32)
+    ks = np.array([13, 23, 5, 32, 26], np.int32)
+    cs = np.array([26, 32, 13, 23, 5, 32, 26, 32, 13, 23, 32, 26], np.int32)   # N = 303
+    A = synth.make_matrix(rng, rs, ks, np.ones((6, 5), bool))
+    B = synth.make_matrix(rng, ks, cs, np.ones((5, 12), bool))
+    got, _ = gpu_multiply("N", "N", 1.0, A, B, 0.0, path="dense", precision="ozaki")
+    ref, _, _ = ozaki_ref(A, B, None, 1.0, 0.0, 7)
+    assert_same_pattern(got, ref)
+    assert np.array_equal(got.data, ref.data)
+    Cm = synth.make_matrix(rng, rs, cs, synth.bernoulli_mask(rng, 6, 12, 0.5))
+    got, _ = gpu_multiply("N", "N", 1.0, A, B, 0.5, Cm, path="dense", precision="ozaki")
+    ref, _, _ = ozaki_ref(A, B, Cm, 1.0, 0.5, 7)
+    assert_same_pattern(got, ref)
+    assert np.array_equal(got.data, ref.data)
