@@ -170,8 +170,8 @@ __global__ void __launch_bounds__(128) k_dgemm_dmma(int64_t M, int64_t N, int64_
                 int64_t r = m0 + wm + a * 8 + (lane >> 2);
                 int64_t c = n0 + wn + b * 8 + 2 * (lane & 3) + h;
                 if (r < M && c < N) {
-                    double v = __dmul_rn(alpha, acc[a][b][h]);
-                    if (beta != 0.0) v = __dadd_rn(v, __dmul_rn(beta, C[r + c * ldc]));
+                    const double v = beta != 0.0 ? blas_update(alpha, acc[a][b][h], beta, C[r + c * ldc])
+                                                 : blas_scale(alpha, acc[a][b][h]);
                     C[r + c * ldc] = v;
                 }
             }

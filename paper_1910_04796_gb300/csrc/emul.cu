@@ -162,9 +162,8 @@ __global__ void k_recombine(int64_t M, int64_t N, int s, int ksegs, const double
         for (int k = 0; k < ksegs; k++) g += (long long)ws[((int64_t)(d - 2) * ksegs + k) * stride + idx];
         S += (__int128)g << (7 * (s + 1 - d));
     }
-    double v = __dmul_rn(alpha, emul::round_i128_scaled(S, e[i] + f[j] - 7 * (s + 1)));
-    if (beta != 0.0) v = __dadd_rn(v, __dmul_rn(beta, C[i + j * ldc]));
-    C[i + j * ldc] = v;
+    const double x = emul::round_i128_scaled(S, e[i] + f[j] - 7 * (s + 1));
+    C[i + j * ldc] = beta != 0.0 ? blas_update(alpha, x, beta, C[i + j * ldc]) : blas_scale(alpha, x);
 }
 
 // 2^k as a double for -1022 <= k <= 1023 (exact bit pattern)
@@ -232,9 +231,7 @@ __global__ void __launch_bounds__(256) k_recombine_rm(int64_t M, int64_t N, int 
         const int64_t i = i0 + tx, j = j0 + cc;
         if (i < M && j < N) {
             const int64_t a = out.at(i, j);
-            double v = __dmul_rn(alpha, tile[tx][cc]);
-            if (beta != 0.0) v = __dadd_rn(v, __dmul_rn(beta, out.C[a]));
-            out.C[a] = v;
+            out.C[a] = beta != 0.0 ? blas_update(alpha, tile[tx][cc], beta, out.C[a]) : blas_scale(alpha, tile[tx][cc]);
         }
     }
 }

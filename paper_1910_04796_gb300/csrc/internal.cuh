@@ -178,4 +178,14 @@ int sync_stream();
 
 inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
+// alpha * x + beta * old with each product and the sum rounded once, in that
+// order (the BLAS update of a C element). A factor of exactly 1 is skipped --
+// 1 * x == x for every double, so the result is the same -- which keeps the
+// common alpha = 1 / beta = 1 updates off the narrow FP64 pipe.
+__device__ __forceinline__ double blas_update(double alpha, double x, double beta, double old) {
+    const double ax = alpha == 1.0 ? x : __dmul_rn(alpha, x);
+    return __dadd_rn(ax, beta == 1.0 ? old : __dmul_rn(beta, old));
+}
+__device__ __forceinline__ double blas_scale(double alpha, double x) { return alpha == 1.0 ? x : __dmul_rn(alpha, x); }
+
 }  // namespace dbcsr

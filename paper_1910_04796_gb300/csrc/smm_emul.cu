@@ -293,11 +293,10 @@ __global__ void __launch_bounds__(SE_THREADS) k_smm_emul(SeArgs a) {
                     __int128 Sx = 0;   // exact sum of the level sums, each shifted to its weight
 #pragma unroll
                     for (int d = 0; d < S; d++) Sx += (__int128)gi[d][nt][r] << (7 * (S - 1 - d));
-                    double v = __dmul_rn(
-                        a.alpha, emul::round_i128_scaled(Sx, a.e[rbase + row] + a.f[cbase + colm] - 7 * (S + 1)));
+                    const double x =
+                        emul::round_i128_scaled(Sx, a.e[rbase + row] + a.f[cbase + colm] - 7 * (S + 1));
                     const int64_t eidx = (int64_t)colm * m + row;
-                    if (cold) v = __dadd_rn(v, __dmul_rn(a.beta, cold[eidx]));
-                    cout[eidx] = v;
+                    cout[eidx] = cold ? blas_update(a.alpha, x, a.beta, cold[eidx]) : blas_scale(a.alpha, x);
                 }
             }
     }

@@ -445,9 +445,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_smm_emul_tc(TcArgs a) {
 #pragma unroll
                 for (int d = NU; d < S; d++) V = V * 128 + lv[d][k];
                 const __int128 Sx = (__int128)U * ((__int128)1 << (7 * (S - NU))) + V;
-                double v = __dmul_rn(a.alpha, emul::round_i128_scaled(Sx, ei + fj[k] - 7 * (S + 1)));
-                if (cur.old_off >= 0) v = __dadd_rn(v, __dmul_rn(a.beta, oldv[k]));
-                res[k] = v;
+                const double x = emul::round_i128_scaled(Sx, ei + fj[k] - 7 * (S + 1));
+                res[k] = cur.old_off >= 0 ? blas_update(a.alpha, x, a.beta, oldv[k]) : blas_scale(a.alpha, x);
             }
             if (row_ok) {
                 double* cout = a.Cd + cur.c_off;

@@ -60,6 +60,17 @@ __device__ __forceinline__ void team_sync(int team) {
     }
 }
 
+// brings n elements from p into L1 ahead of their use: one 128-byte line per
+// lane, every address inside the block (a C block has few products, so most
+// operand blocks would otherwise arrive from L2 while the FP64 pipe waits)
+template <typename T>
+__device__ __forceinline__ void prefetch_block(const T* p, int n, int lane) {
+    const char* b = reinterpret_cast<const char*>(p);
+    const int bytes = n * (int)sizeof(T);
+    for (int o = lane * 128; o < bytes; o += 32 * 128) asm volatile("prefetch.global.L1 [%0];" ::"l"(b + o));
+    if (lane == 31 && bytes > 0) asm volatile("prefetch.global.L1 [%0];" ::"l"(b + bytes - 1));
+}
+
 // one team per C block; each lane holds up to Q elements e = lane + 32*q,
 // r = e % m, c = e / m (column-major order within the block). T is the
 // arithmetic type: double (FP64 path) or float (FP32 path: operands read from
@@ -68,6 +79,7 @@ template <typename T, int Q, int TA, int TB, int W>
 __device__ __forceinline__ void smm_body(const SmmArgs& g, const T* __restrict__ adata, const T* __restrict__ bdata,
                                          const uint32_t* __restrict__ list, int64_t nlist, int chunk,
                                          double* s_red) {
+    constexpr int QG = Q < 4 ? Q : 4;                 // elements per inner-loop group
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int team = warp / W, tw = warp % W;        // team in CTA, warp in team
@@ -83,6 +95,8 @@ __device__ __forceinline__ void smm_body(const SmmArgs& g, const T* __restrict__
         const int nbat = (int)min((int64_t)chunk, nlist - lbase);
         int my_m = 1, my_n = 1;
         long long my_p0 = 0, my_p1 = 0, my_coff = 0, my_old = -1;
+        long long my_fa = -1, my_fb = 0;   // operands of this warp's first product of the block
+        int my_fk = 0;
         if (lane < nbat) {
             const int64_t cbl = list ? (int64_t)list[lbase + lane] : lbase + lane;
             my_m = g.rsC[g.c_row[cbl]];
@@ -92,8 +106,24 @@ __device__ __forceinline__ void smm_body(const SmmArgs& g, const T* __restrict__
             my_coff = g.c_off[cbl];
             const int o = g.c_old ? g.c_old[cbl] : -1;
             my_old = (o >= 0) ? (long long)g.Cold_off[o] : -1;
+            if (my_p0 + tw < my_p1) {
+                const int2 pr = g.prod[my_p0 + tw];
+                my_fa = g.A.off[pr.x];
+                my_fk = (int)(g.A.off[pr.x + 1] - my_fa) / my_m;
+                my_fb = g.B.off[pr.y];
+            }
         }
         for (int bt = 0; bt < nbat; bt++) {
+        // first product of the next C block (and of this one at the start of a batch) into L1
+        for (int x = bt == 0 ? 0 : bt + 1; x <= bt + 1 && x < nbat; x++) {
+            const long long fa = __shfl_sync(0xffffffffu, my_fa, x), fb = __shfl_sync(0xffffffffu, my_fb, x);
+            const int fk = __shfl_sync(0xffffffffu, my_fk, x);
+            const int fm = __shfl_sync(0xffffffffu, my_m, x), fn = __shfl_sync(0xffffffffu, my_n, x);
+            if (fa >= 0) {
+                prefetch_block(adata + fa, fm * fk, lane);
+                prefetch_block(bdata + fb, fk * fn, lane);
+            }
+        }
         const int m = __shfl_sync(0xffffffffu, my_m, bt), n = __shfl_sync(0xffffffffu, my_n, bt);
         const int mn = m * n;
         const int64_t p0 = __shfl_sync(0xffffffffu, my_p0, bt), p1 = __shfl_sync(0xffffffffu, my_p1, bt);
@@ -129,22 +159,39 @@ __device__ __forceinline__ void smm_body(const SmmArgs& g, const T* __restrict__
                     const long long ao = __shfl_sync(0xffffffffu, my_ao, t);
                     const long long bo = __shfl_sync(0xffffffffu, my_bo, t);
                     const int kk = __shfl_sync(0xffffffffu, my_kk, t);
+                    if (t + 1 < nb) {   // the next product's blocks into L1
+                        const long long an = __shfl_sync(0xffffffffu, my_ao, t + 1);
+                        const long long bn = __shfl_sync(0xffffffffu, my_bo, t + 1);
+                        const int kn = __shfl_sync(0xffffffffu, my_kk, t + 1);
+                        prefetch_block(adata + an, m * kn, lane);
+                        prefetch_block(bdata + bn, kn * n, lane);
+                    }
                     const T* __restrict__ a = adata + ao;
                     const T* __restrict__ b = bdata + bo;
-                    int aidx[Q], bidx[Q];
-#pragma unroll
-                    for (int q = 0; q < Q; q++) {
-                        aidx[q] = TA ? ro[q] * kk : ro[q];
-                        bidx[q] = TB ? co[q] : co[q] * kk;
-                    }
                     const int astep = TA ? 1 : m;
                     const int bstep = TB ? n : 1;
-                    for (int l = 0; l < kk; l++) {
+                    // the lane's elements in groups of QG, each group a loop over l
+                    // of its own: groups past nq are skipped by a (uniform) branch,
+                    // so at most QG - 1 FMAs per step are issued for nothing.
+                    // Every accumulator still sums l = 0 .. kk-1 in order.
 #pragma unroll
-                        for (int q = 0; q < Q; q++) {
-                            if (q < nq) acc[q] = fma(__ldg(a + aidx[q]), __ldg(b + bidx[q]), acc[q]);
-                            aidx[q] += astep;
-                            bidx[q] += bstep;
+                    for (int q0 = 0; q0 < Q; q0 += QG) {
+                        if (q0 < nq) {
+                            int aidx[QG], bidx[QG];
+#pragma unroll
+                            for (int j = 0; j < QG; j++) {
+                                aidx[j] = TA ? ro[q0 + j] * kk : ro[q0 + j];
+                                bidx[j] = TB ? co[q0 + j] : co[q0 + j] * kk;
+                            }
+                            for (int l = 0; l < kk; l++) {
+#pragma unroll
+                                for (int j = 0; j < QG; j++) {
+                                    if (q0 + j < nq)
+                                        acc[q0 + j] = fma(__ldg(a + aidx[j]), __ldg(b + bidx[j]), acc[q0 + j]);
+                                    aidx[j] += astep;
+                                    bidx[j] += bstep;
+                                }
+                            }
                         }
                     }
                 }
@@ -169,9 +216,8 @@ __device__ __forceinline__ void smm_body(const SmmArgs& g, const T* __restrict__
                 for (int q = 0; q < Q; q++) {
                     const int e = e0 + lane + 32 * q;
                     if (q < nq && e < mn) {
-                        double v = __dmul_rn(g.alpha, (double)acc[q]);
-                        if (cold) v = __dadd_rn(v, __dmul_rn(g.beta, cold[e]));
-                        cout[e] = v;
+                        cout[e] = cold ? blas_update(g.alpha, (double)acc[q], g.beta, cold[e])
+                                       : blas_scale(g.alpha, (double)acc[q]);
                     }
                 }
             }
@@ -180,8 +226,9 @@ __device__ __forceinline__ void smm_body(const SmmArgs& g, const T* __restrict__
     }
 }
 
+// two 256-thread CTAs per SM (at most 128 registers) up to 16 elements per lane
 template <int Q, int TA, int TB, int W>
-__global__ void __launch_bounds__(256) k_smm_fp64(SmmArgs g, const uint32_t* __restrict__ list, int64_t nlist,
+__global__ void __launch_bounds__(256, Q <= 16 ? 2 : 1) k_smm_fp64(SmmArgs g, const uint32_t* __restrict__ list, int64_t nlist,
                                                         int chunk) {
     extern __shared__ double s_red[];                 // [teams][W-1][Q][32] partial sums
     smm_body<double, Q, TA, TB, W>(g, g.A.data, g.B.data, list, nlist, chunk, s_red);
@@ -189,7 +236,7 @@ __global__ void __launch_bounds__(256) k_smm_fp64(SmmArgs g, const uint32_t* __r
 
 // FP32 stack kernel: one warp per C block
 template <int Q, int TA, int TB>
-__global__ void __launch_bounds__(256) k_smm_fp32(SmmArgs g, const uint32_t* __restrict__ list, int64_t nlist,
+__global__ void __launch_bounds__(256, Q <= 16 ? 2 : 1) k_smm_fp32(SmmArgs g, const uint32_t* __restrict__ list, int64_t nlist,
                                                         int chunk) {
     smm_body<float, Q, TA, TB, 1>(g, g.A32, g.B32, list, nlist, chunk, nullptr);
 }
@@ -279,9 +326,8 @@ __global__ void __launch_bounds__(32 * F32_WARPS) k_smm_f32_tile(SmmArgs g, int 
 #pragma unroll
                 for (int i = 0; i < 32; i++) {
                     if (i < m) {
-                        double v = __dmul_rn(g.alpha, (double)acc[i]);
-                        if (cold) v = __dadd_rn(v, __dmul_rn(g.beta, cold[i]));
-                        cout[i] = v;
+                        cout[i] = cold ? blas_update(g.alpha, (double)acc[i], g.beta, cold[i])
+                                       : blas_scale(g.alpha, (double)acc[i]);
                     }
                 }
             }

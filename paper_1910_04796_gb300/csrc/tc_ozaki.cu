@@ -301,9 +301,9 @@ __global__ void __launch_bounds__(TcCfg::THREADS, 1)
                                 const int64_t j = j0 + g * 32 + c;
                                 if (j < p.N) {
                                     double* cp = p.C + i + j * p.ldc;
-                                    double v = __dmul_rn(p.alpha, (double)__uint_as_float(r[c]));
-                                    if (p.beta != 0.0) v = __dadd_rn(v, __dmul_rn(p.beta, *cp));
-                                    *cp = v;
+                                    const double x = (double)__uint_as_float(r[c]);
+                                    *cp = p.beta != 0.0 ? blas_update(p.alpha, x, p.beta, *cp)
+                                                        : blas_scale(p.alpha, x);
                                 }
                             }
                         }
