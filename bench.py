@@ -349,8 +349,18 @@ def main():
     main_ms = statistics.median(mains)
     s2 = dbcsr.stats()
     path_taken = {dbcsr.PATH_DENSE: "dense", dbcsr.PATH_STACKS: "stacks", dbcsr.PATH_HYBRID: "hybrid"}[s2["path"]]
-    if precision == "fp64":
-        bound, unit = "alu" if path_taken == "stacks" else "tensor", "TFLOP/s"
+    if precision == "fp64" and path_taken == "stacks":
+        # DFMA on the CUDA cores' FP64 pipe: SMs x 2 FMAs per clock (the nominal
+        # 1.25 TFLOP/s at 2 070 MHz over 152 SMs) x 2 flops x the SM clock seen under load
+        bound, unit = "alu", "TFLOP/s"
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        mhz = clk.summary().get("sm_mhz") or clk.summary().get("sm_max_mhz") or 2070.0
+        peak = sms * 2 * 2 * mhz * 1e6 / 1e12
+        peak_note = f"FP64 FMA = {sms} SMs x 2 per clock x 2 x {mhz:.0f} MHz"
+        achieved = s2["main_flops"] / (main_ms / 1e3) / 1e12
+    elif precision == "fp64":
+        # FP64 tensor-core MMA (dense) or a mix (hybrid): the measured bf16 rate x the nominal ratio
+        bound, unit = "tensor", "TFLOP/s"
         peak = pk["bf16_tflops"] * NOMINAL["fp64"] / NOMINAL["bf16"]
         peak_note = f"FP64 = {pk_kind} bf16 burst x nominal FP64/bf16 (1.25/2250)"
         achieved = s2["main_flops"] / (main_ms / 1e3) / 1e12

@@ -92,10 +92,11 @@ typedef struct {
     int kernel;        /* FP64 stack kernel: 0 = per-shape table set with
                           dbcsr_set_tuning (variant 0 for untuned shapes);
                           v = 1..4 forces variant v-1 for every block:
-                          0: one warp per C block, 256-thread CTAs;
-                          1: one warp per C block, 128-thread CTAs;
+                          0: one warp per C block;
+                          1: the same as 0 (kept for tables that name it);
                           2: two warps per C block (products split);
                           3: four warps per C block.
+                          Every C block of a multiply runs in one launch.
                           Emulated-FP64 stack kernel: 0 = tcgen05 when every
                           block edge is at least 12, else mma.sync; 1 = mma.sync
                           (blocks padded to 16); 2 = tcgen05 (blocks padded to

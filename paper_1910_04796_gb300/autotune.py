@@ -3,8 +3,8 @@
 The paper's LIBCUSMM (Sec. II) tunes its kernels per block shape (m, n, k)
 over read/write strategy, threads per block, elements per thread and tiling.
 This library's FP64 stack kernels expose a smaller space (team of 1, 2 or 4
-warps per C block; 128- or 256-thread CTAs; see dbcsr_opts.kernel), chosen
-per C-block shape (m, n). For each shape the tuner builds a synthetic
+warps per C block, see dbcsr_opts.kernel; variant 1 runs as variant 0),
+chosen per C-block shape (m, n). For each shape the tuner builds a synthetic
 block-sparse product of that shape (inner sizes from the workload's set),
 times every variant through the C ABI with the library's own CUDA-event
 kernel timer, keeps the fastest and writes the table as JSON:

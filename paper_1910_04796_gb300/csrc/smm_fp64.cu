@@ -21,9 +21,10 @@
 // memory), keeps the C block in registers, and writes alpha*acc + beta*C_old
 // once -- no atomics on C. Each warp fetches the index data of 32 of its
 // products at once (one lane per product) and broadcasts it with shuffles.
-// C blocks are grouped by (variant, elements per lane) so that small blocks
-// run in a low-register instance with many resident warps; work is handed out
-// by an atomic counter per group (persistent grid).
+// All C blocks of a multiply run in one persistent launch: an instance with
+// up to 16 elements per lane (at most 128 registers: two 256-thread CTAs, 16
+// warps per SM), larger blocks in several passes of 16 per lane; work is
+// handed out by atomic counters.
 #include <vector>
 
 #include "internal.cuh"
@@ -33,16 +34,11 @@ namespace dbcsr {
 
 namespace {
 
-// Variants (the autotuner's search space):
-//   0: 1 warp per C block, 256-thread CTAs      1: 1 warp per C block, 128-thread CTAs
-//   2: 2-warp teams, 256-thread CTAs            3: 4-warp teams, 256-thread CTAs
-struct VariantShape {
-    int team_warps;
-    int cta_threads;
-};
-constexpr VariantShape kVariants[SMM_NUM_VARIANTS] = {{1, 256}, {1, 128}, {2, 256}, {4, 256}};
-constexpr int NQ = 6;                         // elements-per-lane classes 1, 2, 4, 8, 16, 32
-constexpr int kQ[NQ] = {1, 2, 4, 8, 16, 32};
+// Variants (the autotuner's search space): warps per C block.
+//   0: 1 warp     1: 1 warp (runs as 0: the single launch has 256-thread
+//                    CTAs; the number stays so that tuning tables keep their meaning)
+//   2: 2-warp teams     3: 4-warp teams
+constexpr int kTeamWarps[SMM_NUM_VARIANTS] = {1, 1, 2, 4};
 
 __host__ __device__ inline int q_class(int mn) {
     const int q = (mn + 31) / 32;
@@ -78,8 +74,8 @@ __device__ __forceinline__ void prefetch_block(const T* p, int n, int lane) {
 template <typename T, int Q, int TA, int TB, int W>
 __device__ __forceinline__ void smm_body(const SmmArgs& g, const T* __restrict__ adata, const T* __restrict__ bdata,
                                          const uint32_t* __restrict__ list, int64_t nlist, int chunk,
-                                         double* s_red) {
-    constexpr int QG = Q < 4 ? Q : 4;                 // elements per inner-loop group
+                                         double* s_red, unsigned long long* counter) {
+    constexpr int QG = Q < 2 ? Q : 2;                 // elements per inner-loop group
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int team = warp / W, tw = warp % W;        // team in CTA, warp in team
@@ -87,7 +83,7 @@ __device__ __forceinline__ void smm_body(const SmmArgs& g, const T* __restrict__
     for (;;) {
         // a team takes 32 consecutive C blocks at a time; lane t fetches block
         // t's index data in parallel, then the blocks are processed in order
-        if (tw == 0 && lane == 0) s_cb[team] = (int)atomicAdd(g.counter, (unsigned long long)chunk);
+        if (tw == 0 && lane == 0) s_cb[team] = (int)atomicAdd(counter, (unsigned long long)chunk);
         team_sync<W>(team);
         const int64_t lbase = s_cb[team];
         team_sync<W>(team);
@@ -226,19 +222,46 @@ __device__ __forceinline__ void smm_body(const SmmArgs& g, const T* __restrict__
     }
 }
 
-// two 256-thread CTAs per SM (at most 128 registers) up to 16 elements per lane
-template <int Q, int TA, int TB, int W>
-__global__ void __launch_bounds__(256, Q <= 16 ? 2 : 1) k_smm_fp64(SmmArgs g, const uint32_t* __restrict__ list, int64_t nlist,
-                                                        int chunk) {
-    extern __shared__ double s_red[];                 // [teams][W-1][Q][32] partial sums
-    smm_body<double, Q, TA, TB, W>(g, g.A.data, g.B.data, list, nlist, chunk, s_red);
+// Every C block of a multiply in one launch. The blocks come in up to three
+// groups by team size (1, 2 or 4 warps per C block, from the tuning table),
+// stored one after the other in `list` (nullptr: one group of team size 1 over
+// blocks 0 .. n_all-1). A CTA works through the groups in order: its teams
+// take chunks of the current group from that group's counter until it is
+// exhausted, then the CTA re-forms its teams for the next group. The group
+// sizes are read on the device, so the launch needs nothing from the host.
+struct SmmGroups {
+    const int* counts;            // C blocks per team size 1, 2, 4 (nullptr: see n_all)
+    int64_t n_all;
+    unsigned long long* ctr;      // one zeroed counter per group
+};
+
+template <int Q, int TA, int TB>
+__global__ void __launch_bounds__(256, Q <= 16 ? 2 : 1)
+    k_smm_fp64_all(SmmArgs g, const uint32_t* __restrict__ list, SmmGroups gr) {
+    extern __shared__ double s_red[];                 // [teams][W-1][Q][32] partial sums, W <= 4
+    int64_t start = 0;
+#pragma unroll 1
+    for (int k = 0; k < 3; k++) {
+        const int64_t cnt = gr.counts ? (int64_t)gr.counts[k] : (k == 0 ? gr.n_all : 0);
+        if (cnt > 0) {
+            const int64_t teams = (int64_t)gridDim.x * (8 >> k);
+            // C blocks per grab: up to 32, at least ~8 grabs per team
+            const int chunk = (int)max((int64_t)1, min((int64_t)32, cnt / (teams * 8)));
+            const uint32_t* l = list ? list + start : nullptr;
+            if (k == 0) smm_body<double, Q, TA, TB, 1>(g, g.A.data, g.B.data, l, cnt, chunk, s_red, gr.ctr);
+            else if (k == 1) smm_body<double, Q, TA, TB, 2>(g, g.A.data, g.B.data, l, cnt, chunk, s_red, gr.ctr + 1);
+            else smm_body<double, Q, TA, TB, 4>(g, g.A.data, g.B.data, l, cnt, chunk, s_red, gr.ctr + 2);
+            __syncthreads();   // every team done with this group's barriers and partial sums
+        }
+        start += cnt;
+    }
 }
 
 // FP32 stack kernel: one warp per C block
 template <int Q, int TA, int TB>
 __global__ void __launch_bounds__(256, Q <= 16 ? 2 : 1) k_smm_fp32(SmmArgs g, const uint32_t* __restrict__ list, int64_t nlist,
                                                         int chunk) {
-    smm_body<float, Q, TA, TB, 1>(g, g.A32, g.B32, list, nlist, chunk, nullptr);
+    smm_body<float, Q, TA, TB, 1>(g, g.A32, g.B32, list, nlist, chunk, nullptr, g.counter);
 }
 
 // FP32 stack kernel for blocks up to 32 x 32: a warp per C block; each
@@ -364,83 +387,79 @@ int launch_fp32(const SmmArgs& g, int qidx, const uint32_t* list, int64_t nlist)
         case 1: return launch_fp32_q<2>(g, list, nlist);
         case 2: return launch_fp32_q<4>(g, list, nlist);
         case 3: return launch_fp32_q<8>(g, list, nlist);
-        case 4: return launch_fp32_q<16>(g, list, nlist);
-        default: return launch_fp32_q<32>(g, list, nlist);
+        default: return launch_fp32_q<16>(g, list, nlist);   // larger blocks: several passes
     }
 }
 
-template <int Q, int W>
-int launch_qw(const SmmArgs& g, const uint32_t* list, int64_t nlist, int threads) {
-    cudaStream_t st = ctx().stream;
-    const int teams_per_cta = threads / (32 * W);
-    int grid = ctx().num_sms * (2048 / threads);
-    if ((int64_t)grid * teams_per_cta > nlist) grid = (int)cdiv(nlist, teams_per_cta);
-    if (grid < 1) return DBCSR_OK;
-    // C blocks per work grab: up to 32, but at least ~4 grabs per team so
-    // that few heavy blocks still spread over all teams
-    const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(32, nlist / ((int64_t)grid * teams_per_cta * 4)));
-    const size_t red = (W > 1) ? (size_t)teams_per_cta * (W - 1) * Q * 32 * sizeof(double) : 0;
-    const int ta = g.A.trans, tb = g.B.trans;
-#define DB_LAUNCH_SMM(TA_, TB_)                                                                             \
-    do {                                                                                                   \
-        if (red > 0)                                                                                       \
-            DB_CUDA(cudaFuncSetAttribute(k_smm_fp64<Q, TA_, TB_, W>,                                       \
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)red));          \
-        k_smm_fp64<Q, TA_, TB_, W><<<grid, threads, red, st>>>(g, list, nlist, chunk);                           \
-    } while (0)
-    if (!ta && !tb) DB_LAUNCH_SMM(0, 0);
-    else if (ta && !tb) DB_LAUNCH_SMM(1, 0);
-    else if (!ta && tb) DB_LAUNCH_SMM(0, 1);
-    else DB_LAUNCH_SMM(1, 1);
-#undef DB_LAUNCH_SMM
-    DB_KCHECK();
-    return DBCSR_OK;
-}
-
-template <int W>
-int launch_w(const SmmArgs& g, const uint32_t* list, int64_t nlist, int threads, int qidx) {
-    switch (qidx) {
-        case 0: return launch_qw<1, W>(g, list, nlist, threads);
-        case 1: return launch_qw<2, W>(g, list, nlist, threads);
-        case 2: return launch_qw<4, W>(g, list, nlist, threads);
-        case 3: return launch_qw<8, W>(g, list, nlist, threads);
-        case 4: return launch_qw<16, W>(g, list, nlist, threads);
-        default: return launch_qw<32, W>(g, list, nlist, threads);   // larger blocks loop over chunks
-    }
-}
-
-int launch_group(const SmmArgs& g, int variant, int qidx, const uint32_t* list, int64_t nlist) {
-    const VariantShape v = kVariants[variant];
-    switch (v.team_warps) {
-        case 1: return launch_w<1>(g, list, nlist, v.cta_threads, qidx);
-        case 2: return launch_w<2>(g, list, nlist, v.cta_threads, qidx);
-        default: return launch_w<4>(g, list, nlist, v.cta_threads, qidx);
-    }
-}
-
-// group key of every C block: variant * NQ + elements-per-lane class
-__global__ void k_classify(int64_t nC, const int* __restrict__ c_row, const int* __restrict__ c_col,
-                           const int64_t* __restrict__ c_pstart, const int* __restrict__ rsC,
-                           const int* __restrict__ csC,
-                           const signed char* __restrict__ table, int tdim, int forced, uint32_t* __restrict__ key,
-                           uint32_t* __restrict__ idx, int* __restrict__ counts) {
+// team-size index of every C block (0: one warp, 1: two, 2: four), from the
+// tuning table or a forced variant; counts aggregated per CTA before the
+// global atomics
+__global__ void k_classify_team(int64_t nC, const int* __restrict__ c_row, const int* __restrict__ c_col,
+                                const int64_t* __restrict__ c_pstart, const int* __restrict__ rsC,
+                                const int* __restrict__ csC, const signed char* __restrict__ table, int tdim,
+                                int forced, uint32_t* __restrict__ key, uint32_t* __restrict__ idx,
+                                int* __restrict__ counts) {
+    __shared__ int sc[3];
+    if (threadIdx.x < 3) sc[threadIdx.x] = 0;
+    __syncthreads();
     const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (b >= nC) return;
-    const int m = rsC[c_row[b]], n = csC[c_col[b]];
-    int v = forced >= 0 ? forced : 0;
-    if (forced < 0 && table && m < tdim && n < tdim) {
-        const int t = table[m * tdim + n];
-        if (t >= 0) v = t;
-        // a team only pays off with at least two products per warp; a C block
-        // with fewer runs on one warp (its team-mates would wait at the barrier)
-        const int64_t nprod = c_pstart[b + 1] - c_pstart[b];
-        const int team_warps = (v == 2) ? 2 : (v == 3) ? 4 : 1;   // kVariants[v].team_warps
-        if (nprod < 2 * team_warps) v = 0;
+    if (b < nC) {
+        const int m = rsC[c_row[b]], n = csC[c_col[b]];
+        int v = forced >= 0 ? forced : 0;
+        if (forced < 0 && table && m < tdim && n < tdim) {
+            const int t = table[m * tdim + n];
+            if (t >= 0) v = t;
+            // a team only pays off with at least two products per warp; a C block
+            // with fewer runs on one warp (its team-mates would wait at the barrier)
+            const int64_t nprod = c_pstart[b + 1] - c_pstart[b];
+            if (nprod < 2 * ((v == 2) ? 2 : (v == 3) ? 4 : 1)) v = 0;   // kTeamWarps[v]
+        }
+        const int t = (v == 2) ? 1 : (v == 3) ? 2 : 0;                   // team size 1, 2, 4
+        key[b] = (uint32_t)t;
+        idx[b] = (uint32_t)b;
+        atomicAdd(&sc[t], 1);
     }
-    const int k = v * NQ + q_class(m * n);
-    key[b] = (uint32_t)k;
-    idx[b] = (uint32_t)b;
-    atomicAdd(&counts[k], 1);
+    __syncthreads();
+    if (threadIdx.x < 3 && sc[threadIdx.x]) atomicAdd(&counts[threadIdx.x], sc[threadIdx.x]);
+}
+
+template <int Q>
+int launch_all_q(const SmmArgs& g, const uint32_t* list, const SmmGroups& gr) {
+    cudaStream_t st = ctx().stream;
+    const size_t red = (size_t)2 * 3 * Q * 32 * sizeof(double);   // two 4-warp teams per CTA
+    const int ta = g.A.trans, tb = g.B.trans;
+    static int occ[4] = {0, 0, 0, 0};   // resident CTAs per SM of each instance, from its first launch
+    auto go = [&](auto kern, int which) -> int {
+        if (occ[which] == 0) {
+            DB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)red));
+            int o = 0;
+            DB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, 256, red));
+            occ[which] = o > 0 ? o : 1;
+        }
+        int64_t grid = (int64_t)ctx().num_sms * occ[which];
+        const int64_t nC = g.nC;
+        if (grid > (nC + 1) / 2) grid = (nC + 1) / 2;   // at least two C blocks per CTA
+        kern<<<(unsigned)grid, 256, red, st>>>(g, list, gr);
+        DB_KCHECK();
+        return DBCSR_OK;
+    };
+    if (!ta && !tb) return go(k_smm_fp64_all<Q, 0, 0>, 0);
+    if (ta && !tb) return go(k_smm_fp64_all<Q, 1, 0>, 1);
+    if (!ta && tb) return go(k_smm_fp64_all<Q, 0, 1>, 2);
+    return go(k_smm_fp64_all<Q, 1, 1>, 3);
+}
+
+// the one launch over all C blocks; elements per lane from the largest C
+// block, at most 16 (larger blocks take several passes: 16 warps per SM beat
+// 8 warps holding 32 elements per lane, measured)
+int launch_all(const SmmArgs& g, int max_mn, const uint32_t* list, const SmmGroups& gr) {
+    switch (q_class(max_mn)) {
+        case 0: return launch_all_q<1>(g, list, gr);
+        case 1: return launch_all_q<2>(g, list, gr);
+        case 2: return launch_all_q<4>(g, list, gr);
+        case 3: return launch_all_q<8>(g, list, gr);
+        default: return launch_all_q<16>(g, list, gr);
+    }
 }
 
 // (m, n) -> variant table set by dbcsr_set_tuning; -1 = default
@@ -465,54 +484,42 @@ int smm_set_table(const int* m, const int* n, const int* variant, int count) {
 
 int smm_fp64_generic(const SmmArgs& g, int max_mn) {
     if (g.nC == 0) return DBCSR_OK;
-    return launch_group(g, 0, q_class(max_mn), nullptr, g.nC);
+    return launch_all(g, max_mn, nullptr, SmmGroups{nullptr, g.nC, g.counter});
 }
 
 // kernel: 0 = tuned table (variant 0 for untuned shapes), v >= 1 = force variant v-1.
-// C blocks are grouped by (variant, elements-per-lane class); one launch per group.
+// One launch: C blocks grouped by team size on the device, see k_smm_fp64_all.
 int smm_fp64_dispatch(const SmmArgs& g, int max_mn, int kernel) {
     if (g.nC == 0) return DBCSR_OK;
     if (kernel < 0 || kernel > SMM_NUM_VARIANTS) return fail(DBCSR_ERR_ARG, "unknown stack kernel variant");
     if (g.nC >= INT32_MAX) return fail(DBCSR_ERR_OVERFLOW, "stack kernels: too many C blocks");
-    cudaStream_t st = ctx().stream;
-    constexpr int NK = SMM_NUM_VARIANTS * NQ;
     const bool use_table = kernel == 0 && g_table_used;
+    const int forced = kernel >= 1 ? kernel - 1 : -1;
+    if (!use_table && (forced < 0 || kTeamWarps[forced] == 1))
+        return launch_all(g, max_mn, nullptr, SmmGroups{nullptr, g.nC, g.counter});
+    cudaStream_t st = ctx().stream;
     DBuf<signed char> table;
     DBuf<uint32_t> key, idx;
     DBuf<int> counts;
+    DBuf<unsigned long long> ctr;
     if (use_table) {
         DB_TRY(table.alloc(TDIM * TDIM));
         DB_CUDA(cudaMemcpyAsync(table.p, g_table.data(), TDIM * TDIM, cudaMemcpyHostToDevice, st));
     }
     DB_TRY(key.alloc(g.nC));
     DB_TRY(idx.alloc(g.nC));
-    DB_TRY(counts.alloc(NK));
-    DB_CUDA(cudaMemsetAsync(counts.p, 0, sizeof(int) * NK, st));
-    k_classify<<<(unsigned)cdiv(g.nC, 256), 256, 0, st>>>(g.nC, g.c_row, g.c_col, g.c_pstart, g.rsC, g.csC,
-                                                          use_table ? table.p : nullptr, TDIM,
-                                                          kernel >= 1 ? kernel - 1 : -1, key.p, idx.p, counts.p);
+    DB_TRY(counts.alloc(3));
+    DB_TRY(ctr.alloc(3));
+    DB_CUDA(cudaMemsetAsync(counts.p, 0, sizeof(int) * 3, st));
+    DB_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(unsigned long long) * 3, st));
+    k_classify_team<<<(unsigned)cdiv(g.nC, 256), 256, 0, st>>>(g.nC, g.c_row, g.c_col, g.c_pstart, g.rsC, g.csC,
+                                                               use_table ? table.p : nullptr, TDIM, forced, key.p,
+                                                               idx.p, counts.p);
     DB_KCHECK();
-    std::vector<int> h_counts(NK);
-    DB_CUDA(cudaMemcpyAsync(h_counts.data(), counts.p, sizeof(int) * NK, cudaMemcpyDeviceToHost, st));
-    DB_CUDA(cudaStreamSynchronize(st));
-    int used = 0, only = 0;
-    for (int k = 0; k < NK; k++)
-        if (h_counts[k]) { used++; only = k; }
-    if (used <= 1) return launch_group(g, only / NQ, only % NQ, nullptr, g.nC);
-    // stable sort of the C blocks by group: each group's blocks keep CSR order
-    DB_TRY(radix_sort_u32(key.p, idx.p, g.nC, 8));
-    DBuf<unsigned long long> ctr;
-    DB_TRY(ctr.alloc(NK));
-    DB_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(unsigned long long) * NK, st));
-    int64_t start = 0;
-    for (int k = 0; k < NK; k++) {
-        if (!h_counts[k]) continue;
-        SmmArgs gk = g;
-        gk.counter = ctr.p + k;
-        DB_TRY(launch_group(gk, k / NQ, k % NQ, idx.p + start, h_counts[k]));
-        start += h_counts[k];
-    }
-    return DBCSR_OK;
+    // stable sort by team size: each group's blocks keep CSR order (a forced
+    // variant gives one group in CSR order: no sort)
+    if (use_table) DB_TRY(radix_sort_u32(key.p, idx.p, g.nC, 8));
+    return launch_all(g, max_mn, use_table ? idx.p : nullptr, SmmGroups{counts.p, 0, ctr.p});
 }
 
 int to_f32(const double* in, int64_t n, float* out) {
@@ -523,8 +530,8 @@ int to_f32(const double* in, int64_t n, float* out) {
     return DBCSR_OK;
 }
 
-// FP32 stack kernels: blocks up to 32 x 32 on the shared-memory kernel (one
-// launch), larger ones grouped by elements-per-lane class, one warp each.
+// FP32 stack kernels: blocks up to 32 x 32 on the shared-memory kernel, larger
+// ones on the generic body, one warp each; one launch either way.
 int smm_fp32_dispatch(const SmmArgs& g, int max_mn, int max_edge) {
     if (g.nC == 0) return DBCSR_OK;
     if (max_edge <= 32) {
@@ -548,37 +555,8 @@ int smm_fp32_dispatch(const SmmArgs& g, int max_mn, int max_edge) {
         return DBCSR_OK;
     }
     if (g.nC >= INT32_MAX) return fail(DBCSR_ERR_OVERFLOW, "stack kernels: too many C blocks");
-    cudaStream_t st = ctx().stream;
-    DBuf<uint32_t> key, idx;
-    DBuf<int> counts;
-    DB_TRY(key.alloc(g.nC));
-    DB_TRY(idx.alloc(g.nC));
-    DB_TRY(counts.alloc(NQ));
-    DB_CUDA(cudaMemsetAsync(counts.p, 0, sizeof(int) * NQ, st));
-    k_classify<<<(unsigned)cdiv(g.nC, 256), 256, 0, st>>>(g.nC, g.c_row, g.c_col, g.c_pstart, g.rsC, g.csC, nullptr,
-                                                          TDIM, 0, key.p, idx.p, counts.p);
-    DB_KCHECK();
-    std::vector<int> h_counts(NQ);
-    DB_CUDA(cudaMemcpyAsync(h_counts.data(), counts.p, sizeof(int) * NQ, cudaMemcpyDeviceToHost, st));
-    DB_CUDA(cudaStreamSynchronize(st));
-    int used = 0, only = 0;
-    for (int k = 0; k < NQ; k++)
-        if (h_counts[k]) { used++; only = k; }
-    (void)max_mn;
-    if (used <= 1) return launch_fp32(g, only, nullptr, g.nC);
-    DB_TRY(radix_sort_u32(key.p, idx.p, g.nC, 8));
-    DBuf<unsigned long long> ctr;
-    DB_TRY(ctr.alloc(NQ));
-    DB_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(unsigned long long) * NQ, st));
-    int64_t start = 0;
-    for (int k = 0; k < NQ; k++) {
-        if (!h_counts[k]) continue;
-        SmmArgs gk = g;
-        gk.counter = ctr.p + k;
-        DB_TRY(launch_fp32(gk, k, idx.p + start, h_counts[k]));
-        start += h_counts[k];
-    }
-    return DBCSR_OK;
+    // larger blocks: one launch, up to 16 elements per lane (more in passes)
+    return launch_fp32(g, q_class(max_mn), nullptr, g.nC);
 }
 
 }  // namespace dbcsr

@@ -21,20 +21,35 @@ from dataclasses import dataclass, field
 import numpy as np
 
 # (warps per C block, threads per CTA) of the FP64 stack-kernel variants
-# (dbcsr_opts.kernel = variant + 1)
-VARIANTS = ((1, 256), (1, 128), (2, 256), (4, 256))
+# (dbcsr_opts.kernel = variant + 1); variant 1 runs as variant 0 (the single
+# persistent launch has 256-thread CTAs)
+VARIANTS = ((1, 256), (1, 256), (2, 256), (4, 256))
 FEATURES = ("m", "n", "k", "mn", "mnk", "q", "lane_fill", "passes", "team_warps", "cta_threads",
             "teams_per_cta", "k_per_warp", "bytes_per_product", "flops_per_byte", "regs_class",
             "acc_per_lane")
+Q_MAX = 16          # elements per lane of the largest kernel instance
+GROUP = 2           # elements per inner-loop group (FMAs issue for whole groups)
 
 
 def q_of(mn: int) -> int:
-    """Elements per lane the kernel instantiates for an m*n C block: 1, 2, 4, .., 32."""
+    """Elements per lane the kernel instantiates for an m*n C block: 1, 2, 4, 8, 16."""
     q = (mn + 31) // 32
-    for c in (1, 2, 4, 8, 16):
+    for c in (1, 2, 4, 8):
         if q <= c:
             return c
-    return 32
+    return Q_MAX
+
+
+def issued_slots(mn: int, q: int) -> int:
+    """Lane slots of the FMAs issued per inner step over the whole C block:
+    each pass covers up to 32 q elements, in groups of GROUP per lane."""
+    slots, e0 = 0, 0
+    while e0 < mn:
+        nq = min(q, -(-(mn - e0) // 32))
+        g = min(GROUP, q)
+        slots += 32 * g * -(-nq // g)
+        e0 += 32 * q
+    return slots
 
 
 def features(m: int, n: int, k: int, variant: int) -> np.ndarray:
@@ -43,7 +58,7 @@ def features(m: int, n: int, k: int, variant: int) -> np.ndarray:
     mn = m * n
     q = q_of(mn)
     passes = math.ceil(mn / (32 * q))          # sweeps of the lane grid over the C block
-    lane_fill = mn / (passes * 32 * q)         # useful fraction of the lane slots
+    lane_fill = mn / issued_slots(mn, q)       # useful fraction of the issued lane slots
     bytes_pp = 8.0 * (m * k + k * n)           # A and B block per product
     return np.array([
         m, n, k, mn, mn * k, q, lane_fill, passes, w, t, t // (32 * w), k / w, bytes_pp,

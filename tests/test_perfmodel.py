@@ -16,10 +16,14 @@ from paper_1910_04796_gb300 import perfmodel as P
 
 def test_q_and_lane_fill():
     assert [P.q_of(x) for x in (1, 32, 33, 64, 65, 128, 129, 256, 257, 512, 513, 1024)] == \
-        [1, 1, 2, 2, 4, 4, 8, 8, 16, 16, 32, 32]
+        [1, 1, 2, 2, 4, 4, 8, 8, 16, 16, 16, 16]
     f = dict(zip(P.FEATURES, P.features(13, 23, 5, 2)))
+    # 299 elements: 10 per lane (lanes 12..31 hold 9), issued in 5 groups of 2
     assert f["mn"] == 299 and f["q"] == 16 and f["passes"] == 1
-    assert f["lane_fill"] == pytest.approx(299 / 512)
+    assert f["lane_fill"] == pytest.approx(299 / 320)
+    # 32 x 32: two passes of 16 per lane, every slot used; 5 x 5: one group of one
+    assert P.issued_slots(1024, 16) == 1024 and P.issued_slots(25, 1) == 32
+    assert P.issued_slots(17 * 32 + 1, 16) == 32 * 16 + 32 * 2   # second pass: 33 elements, one group of two
     assert f["team_warps"] == 2 and f["cta_threads"] == 256 and f["teams_per_cta"] == 4
     assert f["bytes_per_product"] == 8 * (13 * 5 + 5 * 23)
 
@@ -58,12 +62,10 @@ def test_root_split_is_brute_force_optimum():
 
 
 def _synthetic_perf(m, n, k, v):
-    # a made-up GPU: wider teams pay off for long inner products of small C blocks,
-    # 128-thread CTAs for tiny blocks; TFLOP/s grows with the lane fill
+    # a made-up GPU: wider teams pay off for long inner products of small C
+    # blocks; TFLOP/s grows with the lane fill
     f = dict(zip(P.FEATURES, P.features(m, n, k, v)))
     base = 0.2 + 0.8 * f["lane_fill"] * min(1.0, f["mnk"] / 4000.0)
-    if v == 1:
-        base *= 1.15 if f["mn"] <= 32 else 0.9
     if v in (2, 3):
         base *= (1.0 + 0.02 * f["k_per_warp"]) if f["mn"] <= 128 else 0.8
     return base
