@@ -46,6 +46,28 @@ def test_mixed_variant_table():
         dbcsr.set_tuning([])
 
 
+@pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "N"), ("N", "T")])
+def test_mixed_variant_table_integer_exact(ta, tb):
+    # teams of 1, 2 and 4 warps in the same launch (the group sizes are read on
+    # the device), blocks above 16 elements per lane in several passes:
+    # integer-valued inputs make every order of the sums exact
+    setup()
+    sizes = (5, 13, 23, 26, 32, 45)
+    table = [(m, n, (m + 3 * n) % 4) for m in sizes for n in sizes]
+    dbcsr.set_tuning(table)
+    try:
+        rng = np.random.default_rng(821)
+        A, B, Cm = synth.random_small(rng, 14, 30, 13, p=0.6, sizes=sizes, dist="int", with_c=True)
+        As = synth.transpose_blocks(A) if ta == "T" else A
+        Bs = synth.transpose_blocks(B) if tb == "T" else B
+        got, _ = gpu_multiply(ta, tb, 2.0, As, Bs, -1.0, Cm, path="stacks")
+        ref = O.multiply(ta, tb, 2.0, As, Bs, -1.0, Cm)
+        assert_same_pattern(got, ref)
+        assert np.array_equal(got.data, ref.data)
+    finally:
+        dbcsr.set_tuning([])
+
+
 def test_autotune_shape_and_table_roundtrip(tmp_path):
     setup()
     best, res = autotune.tune_shape(13, 22, (5, 13), reps=1)
