@@ -161,6 +161,7 @@ __global__ void __launch_bounds__(128) k_dgemm_dmma(int64_t M, int64_t N, int64_
         __syncthreads();
     }
     // epilogue: element (row = lane>>2, col = 2*(lane&3) + {0,1}) of each fragment
+    const BlasUpd bu(alpha, beta);
 #pragma unroll
     for (int a = 0; a < 4; a++)
 #pragma unroll
@@ -170,9 +171,7 @@ __global__ void __launch_bounds__(128) k_dgemm_dmma(int64_t M, int64_t N, int64_
                 int64_t r = m0 + wm + a * 8 + (lane >> 2);
                 int64_t c = n0 + wn + b * 8 + 2 * (lane & 3) + h;
                 if (r < M && c < N) {
-                    const double v = beta != 0.0 ? blas_update(alpha, acc[a][b][h], beta, C[r + c * ldc])
-                                                 : blas_scale(alpha, acc[a][b][h]);
-                    C[r + c * ldc] = v;
+                    C[r + c * ldc] = bu.old ? bu.update(acc[a][b][h], C[r + c * ldc]) : bu.scale(acc[a][b][h]);
                 }
             }
 }

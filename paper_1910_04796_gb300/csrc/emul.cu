@@ -75,34 +75,8 @@ __global__ void k_exponents(int64_t n, const unsigned long long* __restrict__ bi
     e[i] = ex;
 }
 
-// floor(|x| 2^(7s - e)) with the sign of x, from the bit pattern of x.
-// |x| 2^-e < 1 guarantees the result is below 2^(7s) <= 2^56.
-__device__ __forceinline__ long long fixed_point(double x, int e, int s) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const int ex = (int)((b >> 52) & 0x7ff);
-    unsigned long long m = b & 0xfffffffffffffull;
-    int E;   // |x| = m * 2^E
-    if (ex == 0) {
-        E = -1074;
-    } else {
-        m |= 1ull << 52;
-        E = ex - 1075;
-    }
-    const int sh = E - e + 7 * s;
-    unsigned long long q;
-    if (m == 0) q = 0;
-    else if (sh >= 0) q = m << sh;
-    else if (sh > -64) q = m >> (-sh);
-    else q = 0;
-    return (b >> 63) ? -(long long)q : (long long)q;
-}
-
-__device__ __forceinline__ __nv_bfloat16 slice_bf16(long long q, int t, int s) {
-    const unsigned long long a = (unsigned long long)(q < 0 ? -q : q);
-    int v = (int)((a >> (7 * (s - t))) & 127ull);
-    if (q < 0) v = -v;
-    return __float2bfloat16_rn((float)v);   // |v| <= 127: exact
-}
+using emul::fixed_point;
+using emul::slice_bf16;
 
 // A (column-major M x K) -> SA[t][i][l] (row-major, ldk), zero for l >= K.
 // 32 (rows) x 64 (k) tiles through shared memory so that both sides coalesce.
@@ -163,7 +137,8 @@ __global__ void k_recombine(int64_t M, int64_t N, int s, int ksegs, const double
         S += (__int128)g << (7 * (s + 1 - d));
     }
     const double x = emul::round_i128_scaled(S, e[i] + f[j] - 7 * (s + 1));
-    C[i + j * ldc] = beta != 0.0 ? blas_update(alpha, x, beta, C[i + j * ldc]) : blas_scale(alpha, x);
+    const BlasUpd bu(alpha, beta);
+    C[i + j * ldc] = bu.old ? bu.update(x, C[i + j * ldc]) : bu.scale(x);
 }
 
 // 2^k as a double for -1022 <= k <= 1023 (exact bit pattern)
@@ -209,31 +184,52 @@ __global__ void __launch_bounds__(256) k_recombine_rm(int64_t M, int64_t N, int 
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
     const int64_t i0 = (int64_t)blockIdx.y * 32, j0 = (int64_t)blockIdx.x * 32;
     const int64_t lstride = M * ldws;
-    for (int r = ty; r < 32; r += 8) {
-        const int64_t i = i0 + r, j = j0 + tx;
-        double acc = 0.0;
-        if (i < M && j < N) {
-            long long U = 0, V = 0;
+    const BlasUpd bu(alpha, beta);
+    // the old C of this thread's four output elements first: its latency hides
+    // behind the level sums
+    int64_t addr[4];
+    double cold[4];
 #pragma unroll
-            for (int d = 0; d < S; d++) {
-                long long g = 0;   // exact: sum over K segments of int32 partial sums
-                for (int k = 0; k < ksegs; k++) g += ws[((int64_t)d * ksegs + k) * lstride + i * ldws + j];
-                if (d < NU) U = U * 128 + g;
-                else V = V * 128 + g;
-            }
-            const __int128 Sx = (__int128)U * ((__int128)1 << (7 * (S - NU))) + V;
-            acc = emul::round_i128_scaled(Sx, e[i] + f[j] - 7 * (S + 1));
+    for (int c = 0; c < 4; c++) {
+        const int64_t i = i0 + tx, j = j0 + ty + 8 * c;
+        addr[c] = (i < M && j < N) ? out.at(i, j) : -1;
+        cold[c] = (bu.old && addr[c] >= 0) ? out.C[addr[c]] : 0.0;
+    }
+    // level sums of the thread's four elements (rows ty + 8 c, column tx), first
+    // K segment: all loads issued before the arithmetic
+    int v[4][S];
+    bool in[4];
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        const int64_t i = i0 + ty + 8 * c, j = j0 + tx;
+        in[c] = i < M && j < N;
+        const int* w = ws + (in[c] ? i * ldws + j : 0);
+#pragma unroll
+        for (int d = 0; d < S; d++) v[c][d] = in[c] ? w[(int64_t)d * ksegs * lstride] : 0;
+    }
+    const int fj = (j0 + tx < N) ? f[j0 + tx] : 0;
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        const int* w = ws + (in[c] ? (i0 + ty + 8 * c) * ldws + j0 + tx : 0);
+        long long U = 0, V = 0;
+#pragma unroll
+        for (int d = 0; d < S; d++) {
+            long long g = v[c][d];   // exact: further K segments summed in int64
+            for (int k = 1; k < ksegs; k++) g += in[c] ? w[((int64_t)d * ksegs + k) * lstride] : 0;
+            if (d < NU) U = U * 128 + g;
+            else V = V * 128 + g;
         }
-        tile[r][tx] = acc;
+        const __int128 Sx = (__int128)U * ((__int128)1 << (7 * (S - NU))) + V;
+        const int64_t i = i0 + ty + 8 * c;
+        tile[ty + 8 * c][tx] = in[c] ? emul::round_i128_scaled(Sx, e[i] + fj - 7 * (S + 1)) : 0.0;
     }
     __syncthreads();
-    for (int cc = ty; cc < 32; cc += 8) {
-        const int64_t i = i0 + tx, j = j0 + cc;
-        if (i < M && j < N) {
-            const int64_t a = out.at(i, j);
-            out.C[a] = beta != 0.0 ? blas_update(alpha, tile[tx][cc], beta, out.C[a]) : blas_scale(alpha, tile[tx][cc]);
+#pragma unroll
+    for (int c = 0; c < 4; c++)
+        if (addr[c] >= 0) {
+            const double x = tile[tx][ty + 8 * c];
+            out.C[addr[c]] = bu.old ? bu.update(x, cold[c]) : bu.scale(x);
         }
-    }
 }
 
 // element-row layout of a fully occupied block matrix (see OzOut)
@@ -252,9 +248,11 @@ __global__ void k_full_rows(int nbr, const int* __restrict__ rs, const int64_t* 
 // Slices of every stored block of one operand, written straight into the
 // dense K-major slice layout S[(t-1) * rows + x][l] (row stride ldk): x is
 // the op() line (row of op(A) / column of op(B)), l the inner index. A warp
-// per block, lanes along l; a block (at most a few KB) stays in L1 while its
-// lines are read, so the strided reads cost little. Two consecutive l per
-// lane (4-byte stores) when the block's first l and its width are even.
+// per block; a line's items (two consecutive l with 4-byte stores when the
+// block's first l, its width and ldk are even, else single l) go to a group
+// of lanes -- the item count rounded up to a power of two -- so that a warp
+// covers 32 / group lines at once. A block (at most a few KB) stays in L1
+// while its lines are read, so the strided reads cost little.
 __global__ void k_slice_blocks(SliceGeom G, const int* __restrict__ ex, int s, int64_t rows, int64_t ldk,
                                __nv_bfloat16* __restrict__ S) {
     const int lane = threadIdx.x & 31;
@@ -268,21 +266,25 @@ __global__ void k_slice_blocks(SliceGeom G, const int* __restrict__ ex, int s, i
         const int64_t lbase = G.x_is_row ? G.coff[G.col[b]] : G.roff[G.row_of[b]];
         const double* d = G.data + G.off[b];
         const bool pairs = ((lbase | L | ldk) & 1) == 0;
-        for (int x = 0; x < X; x++) {
+        const int items = pairs ? L >> 1 : L;   // per line
+        int grp = 1;                             // lanes per line
+        while (grp < items && grp < 32) grp <<= 1;
+        const int sub = lane & (grp - 1), xr = lane / grp, lines = 32 / grp;
+        for (int x = xr; x < X; x += lines) {
             const int e = ex[xbase + x];
             __nv_bfloat16* o = S + (xbase + x) * ldk + lbase;
-            if (pairs) {
-                for (int l = 2 * lane; l < L; l += 64) {
-                    const long long q0 = fixed_point(d[(int64_t)x * xs + (int64_t)l * ls], e, s);
-                    const long long q1 = fixed_point(d[(int64_t)x * xs + (int64_t)(l + 1) * ls], e, s);
+            const double* dx = d + (int64_t)x * xs;
+            for (int it = sub; it < items; it += grp) {
+                if (pairs) {
+                    const int l = 2 * it;
+                    const long long q0 = fixed_point(dx[(int64_t)l * ls], e, s);
+                    const long long q1 = fixed_point(dx[(int64_t)(l + 1) * ls], e, s);
                     for (int t = 1; t <= s; t++)
                         *reinterpret_cast<__nv_bfloat162*>(o + (int64_t)(t - 1) * plane + l) =
                             __halves2bfloat162(slice_bf16(q0, t, s), slice_bf16(q1, t, s));
-                }
-            } else {
-                for (int l = lane; l < L; l += 32) {
-                    const long long q = fixed_point(d[(int64_t)x * xs + (int64_t)l * ls], e, s);
-                    for (int t = 1; t <= s; t++) o[(int64_t)(t - 1) * plane + l] = slice_bf16(q, t, s);
+                } else {
+                    const long long q = fixed_point(dx[(int64_t)it * ls], e, s);
+                    for (int t = 1; t <= s; t++) o[(int64_t)(t - 1) * plane + it] = slice_bf16(q, t, s);
                 }
             }
         }

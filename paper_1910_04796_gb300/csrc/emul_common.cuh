@@ -31,12 +31,17 @@ __device__ __forceinline__ long long fixed_point(double x, int e, int s) {
     return (b >> 63) ? -(long long)q : (long long)q;
 }
 
-// slice t (1-based) of the fixed-point value q, as an exact bf16
+// slice t (1-based) of the fixed-point value q, as an exact bf16. The integer
+// v (|v| <= 127) becomes a float without the quarter-rate conversion unit:
+// the bit pattern of 1.5 * 2^23 plus v is the float 1.5 * 2^23 + v (ulp 1 in
+// [2^23, 2^24) for |v| < 2^22), and subtracting 1.5 * 2^23 is exact. v has at
+// most 7 significant bits, so the float's upper half is its exact bf16.
 __device__ __forceinline__ __nv_bfloat16 slice_bf16(long long q, int t, int s) {
     const unsigned long long a = (unsigned long long)(q < 0 ? -q : q);
     int v = (int)((a >> (7 * (s - t))) & 127ull);
     if (q < 0) v = -v;
-    return __float2bfloat16_rn((float)v);   // |v| <= 127: exact
+    const float fv = __int_as_float(0x4B400000 + v) - 12582912.0f;
+    return __ushort_as_bfloat16((unsigned short)(__float_as_uint(fv) >> 16));
 }
 
 // frexp exponent of a magnitude given by its bit pattern (0 for zero)
@@ -49,6 +54,14 @@ __device__ __forceinline__ int exponent_of_bits(unsigned long long bits) {
 
 __device__ __forceinline__ unsigned long long abs_bits(double x) {
     return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+
+// mant * 2^ex * 2^k with the sign, for results outside the normal range. A
+// call of its own: inlined, the compiler would turn the rare branch into
+// predicated FP64 instructions that occupy the FP64 pipe for every element.
+static __device__ __noinline__ double scaled_outside_normal(unsigned long long mant, int ex, int k, bool neg) {
+    const double r = ldexp((double)mant, ex);   // exact: mant < 2^53
+    return ldexp(neg ? -r : r, k);
 }
 
 // Recombination of the level sums: S = sum_d G_d 2^(7(s+1-d)) is an exact
@@ -106,8 +119,7 @@ __device__ __forceinline__ double round_i128_scaled(__int128 S, int k) {
                                         ((unsigned long long)(E + 1023) << 52) | (mant & 0xfffffffffffffull);
         return __longlong_as_double((long long)bits);
     }
-    const double r = ldexp((double)mant, ex);   // exact: |S| < 2^127
-    return ldexp(neg ? -r : r, k);
+    return scaled_outside_normal(mant, ex, k, neg);
 }
 
 }  // namespace emul

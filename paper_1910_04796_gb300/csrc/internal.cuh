@@ -178,14 +178,40 @@ int sync_stream();
 
 inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
-// alpha * x + beta * old with each product and the sum rounded once, in that
-// order (the BLAS update of a C element). A factor of exactly 1 is skipped --
+// The BLAS update of a C element: alpha * x + beta * old, each product and
+// the sum rounded once, in that order. A factor of exactly 1 is skipped --
 // 1 * x == x for every double, so the result is the same -- which keeps the
-// common alpha = 1 / beta = 1 updates off the narrow FP64 pipe.
-__device__ __forceinline__ double blas_update(double alpha, double x, double beta, double old) {
-    const double ax = alpha == 1.0 ? x : __dmul_rn(alpha, x);
-    return __dadd_rn(ax, beta == 1.0 ? old : __dmul_rn(beta, old));
+// common alpha = 1 / beta = 1 updates off the narrow FP64 pipe. The tests on
+// alpha and beta compare bit patterns (integer instructions: the compiler may
+// re-evaluate them per element, and FP64 comparisons would take the FP64 pipe).
+__device__ __forceinline__ unsigned long long dbits(double x) {
+#ifdef __CUDA_ARCH__
+    return (unsigned long long)__double_as_longlong(x);
+#else
+    return 0ull;   // host pass of a device-only helper: never executed
+#endif
 }
-__device__ __forceinline__ double blas_scale(double alpha, double x) { return alpha == 1.0 ? x : __dmul_rn(alpha, x); }
+
+struct BlasUpd {
+    double alpha, beta;
+    bool a1, b1, old;   // alpha == 1, beta == 1, beta != 0 (the old C is read)
+    __device__ __forceinline__ BlasUpd(double a, double b)
+        : alpha(a),
+          beta(b),
+          a1(dbits(a) == 0x3FF0000000000000ull),
+          b1(dbits(b) == 0x3FF0000000000000ull),
+          old((dbits(b) << 1) != 0ull) {}   // +-0: no old C
+    // the general forms are calls: inlined, the compiler evaluates both arms
+    // of the selects and the skipped multiplies still occupy the FP64 pipe
+    __device__ __forceinline__ double scale(double x) const { return a1 ? x : scale_any(alpha, x); }
+    __device__ __forceinline__ double update(double x, double c) const {
+        return (a1 && b1) ? __dadd_rn(x, c) : update_any(alpha, x, beta, c, a1, b1);
+    }
+    static __device__ __noinline__ double scale_any(double alpha, double x) { return __dmul_rn(alpha, x); }
+    static __device__ __noinline__ double update_any(double alpha, double x, double beta, double c, bool a1,
+                                                     bool b1) {
+        return __dadd_rn(a1 ? x : __dmul_rn(alpha, x), b1 ? c : __dmul_rn(beta, c));
+    }
+};
 
 }  // namespace dbcsr

@@ -185,6 +185,7 @@ __global__ void __launch_bounds__(SE_THREADS) k_smm_emul(SeArgs a) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int wm = warp & 1, wn = warp >> 1;
     const int g = lane >> 2, q = lane & 3;
+    const BlasUpd bu(a.alpha, a.beta);
     for (;;) {
         if (tid == 0) s_cb = (int)atomicAdd(a.counter, 1ULL);
         __syncthreads();
@@ -296,7 +297,7 @@ __global__ void __launch_bounds__(SE_THREADS) k_smm_emul(SeArgs a) {
                     const double x =
                         emul::round_i128_scaled(Sx, a.e[rbase + row] + a.f[cbase + colm] - 7 * (S + 1));
                     const int64_t eidx = (int64_t)colm * m + row;
-                    cout[eidx] = cold ? blas_update(a.alpha, x, a.beta, cold[eidx]) : blas_scale(a.alpha, x);
+                    cout[eidx] = cold ? bu.update(x, cold[eidx]) : bu.scale(x);
                 }
             }
     }

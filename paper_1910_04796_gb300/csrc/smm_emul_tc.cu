@@ -334,6 +334,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_smm_emul_tc(TcArgs a) {
         // of every 32-column accumulator block; in the sum and the final
         // stage thread (warp (q, r), lane) owns row i = lane, columns 4 ep .. 4 ep + 3
         const int q = warp & 3, r = (warp - 2) >> 2, ep = q * TC_R + r;
+        const BlasUpd bu(a.alpha, a.beta);
         const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(r * TC_COLS);
         const int t1 = q + 1, t2 = S - q;                 // A slices of quadrant q in G1 and G2
         const bool has2 = (G::N2 > 0) && (t2 >= 5);
@@ -446,7 +447,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_smm_emul_tc(TcArgs a) {
                 for (int d = NU; d < S; d++) V = V * 128 + lv[d][k];
                 const __int128 Sx = (__int128)U * ((__int128)1 << (7 * (S - NU))) + V;
                 const double x = emul::round_i128_scaled(Sx, ei + fj[k] - 7 * (S + 1));
-                res[k] = cur.old_off >= 0 ? blas_update(a.alpha, x, a.beta, oldv[k]) : blas_scale(a.alpha, x);
+                res[k] = cur.old_off >= 0 ? bu.update(x, oldv[k]) : bu.scale(x);
             }
             if (row_ok) {
                 double* cout = a.Cd + cur.c_off;

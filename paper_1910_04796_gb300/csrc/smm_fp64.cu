@@ -76,6 +76,7 @@ __device__ __forceinline__ void smm_body(const SmmArgs& g, const T* __restrict__
                                          const uint32_t* __restrict__ list, int64_t nlist, int chunk,
                                          double* s_red, unsigned long long* counter) {
     constexpr int QG = Q < 2 ? Q : 2;                 // elements per inner-loop group
+    const BlasUpd bu(g.alpha, g.beta);
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int team = warp / W, tw = warp % W;        // team in CTA, warp in team
@@ -212,8 +213,7 @@ __device__ __forceinline__ void smm_body(const SmmArgs& g, const T* __restrict__
                 for (int q = 0; q < Q; q++) {
                     const int e = e0 + lane + 32 * q;
                     if (q < nq && e < mn) {
-                        cout[e] = cold ? blas_update(g.alpha, (double)acc[q], g.beta, cold[e])
-                                       : blas_scale(g.alpha, (double)acc[q]);
+                        cout[e] = cold ? bu.update((double)acc[q], cold[e]) : bu.scale((double)acc[q]);
                     }
                 }
             }
@@ -285,6 +285,7 @@ __global__ void __launch_bounds__(32 * F32_WARPS) k_smm_f32_tile(SmmArgs g, int 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float* a_s = f32_smem + warp * F32_WARP_FLOATS;   // A(i, l) at l * 36 + i
     float* b_s = a_s + 32 * F32_ASTRIDE;               // B(l, j) at j * 33 + l
+    const BlasUpd bu(g.alpha, g.beta);
     for (;;) {
         if (lane == 0) s_cb[warp] = (int)atomicAdd(g.counter, (unsigned long long)chunk);
         __syncwarp();
@@ -349,8 +350,7 @@ __global__ void __launch_bounds__(32 * F32_WARPS) k_smm_f32_tile(SmmArgs g, int 
 #pragma unroll
                 for (int i = 0; i < 32; i++) {
                     if (i < m) {
-                        cout[i] = cold ? blas_update(g.alpha, (double)acc[i], g.beta, cold[i])
-                                       : blas_scale(g.alpha, (double)acc[i]);
+                        cout[i] = cold ? bu.update((double)acc[i], cold[i]) : bu.scale((double)acc[i]);
                     }
                 }
             }

@@ -201,6 +201,7 @@ __global__ void __launch_bounds__(W_THREADS, 1)
     } else {
         asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(W_REGS_EPI));
         // --------------------------------------------------------- epilogue
+        const BlasUpd bu(p.alpha, p.beta);
         const int q = warp & 3;
         const int half = (warp - 4) >> 2;
         const int row = q * 32 + lane;
@@ -252,7 +253,7 @@ __global__ void __launch_bounds__(W_THREADS, 1)
                             if (j < p.N) {
                                 double* cp = p.C + i + j * p.ldc;
                                 const double x = (double)__uint_as_float(r[c]);
-                                *cp = p.beta != 0.0 ? blas_update(p.alpha, x, p.beta, *cp) : blas_scale(p.alpha, x);
+                                *cp = bu.old ? bu.update(x, *cp) : bu.scale(x);
                             }
                         }
                     }

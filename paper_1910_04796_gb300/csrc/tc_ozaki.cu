@@ -249,6 +249,7 @@ __global__ void __launch_bounds__(TcCfg::THREADS, 1)
         }
     } else {
         // --------------------------------------------------------- epilogue
+        const BlasUpd bu(p.alpha, p.beta);
         const int q = warp & 3;                   // TMEM lane quadrant this warp may access
         const int row = q * 32 + lane;
         const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
@@ -302,8 +303,7 @@ __global__ void __launch_bounds__(TcCfg::THREADS, 1)
                                 if (j < p.N) {
                                     double* cp = p.C + i + j * p.ldc;
                                     const double x = (double)__uint_as_float(r[c]);
-                                    *cp = p.beta != 0.0 ? blas_update(p.alpha, x, p.beta, *cp)
-                                                        : blas_scale(p.alpha, x);
+                                    *cp = bu.old ? bu.update(x, *cp) : bu.scale(x);
                                 }
                             }
                         }
