@@ -291,6 +291,51 @@ __global__ void k_slice_blocks(SliceGeom G, const int* __restrict__ ex, int s, i
     }
 }
 
+// Slices of a fully occupied matrix whose block rows and block columns each
+// have a single size, straight into the K-major slice layout. A warp takes one
+// op() line x and a run of 64 consecutive l (two per lane), so every slice row
+// segment is written as whole 128-byte lines; consecutive warps take
+// consecutive lines of the same run, which read the same blocks (L1 hits).
+// The element's block is found arithmetically: block (r, c) of the CSR-ordered
+// full matrix starts at (r * nbc + c) * X * L.
+struct UniGeom {
+    const double* data;
+    int X, L;          // block extent along x and along l
+    int64_t nbc;       // stored block columns
+    int x_is_row;      // x runs over stored rows (else stored columns)
+    int64_t nlines;    // op() lines
+    int64_t K;         // inner length
+};
+
+__device__ __forceinline__ double uni_elem(const UniGeom& G, unsigned bx, unsigned xw, unsigned l) {
+    const unsigned bl = l / (unsigned)G.L, lw = l - bl * (unsigned)G.L;
+    const int64_t blk = G.x_is_row ? (int64_t)bx * G.nbc + bl : (int64_t)bl * G.nbc + bx;
+    const int64_t in_blk = G.x_is_row ? (int64_t)xw + (int64_t)lw * G.X : (int64_t)lw + (int64_t)xw * G.L;
+    return G.data[blk * G.X * G.L + in_blk];
+}
+
+__global__ void __launch_bounds__(256) k_slice_uniform(UniGeom G, const int* __restrict__ ex, int s, int64_t ldk,
+                                                       __nv_bfloat16* __restrict__ S) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nruns = (G.K + 63) / 64;
+    const int64_t plane = G.nlines * ldk;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; w < G.nlines * nruns; w += nw) {
+        const int64_t x = w % G.nlines, run = w / G.nlines;
+        const int64_t l = run * 64 + 2 * lane;
+        if (l >= G.K) continue;
+        const int e = ex[x];
+        const unsigned bx = (unsigned)(x / G.X), xw = (unsigned)(x - (int64_t)bx * G.X);
+        const long long q0 = fixed_point(uni_elem(G, bx, xw, (unsigned)l), e, s);
+        // l + 1 = K is K padding: zero (ldk >= K is a multiple of 64, so it is inside the row)
+        const long long q1 = l + 1 < G.K ? fixed_point(uni_elem(G, bx, xw, (unsigned)l + 1u), e, s) : 0;
+        __nv_bfloat16* o = S + x * ldk + l;
+        for (int t = 1; t <= s; t++)
+            *reinterpret_cast<__nv_bfloat162*>(o + (int64_t)(t - 1) * plane) =
+                __halves2bfloat162(slice_bf16(q0, t, s), slice_bf16(q1, t, s));
+    }
+}
+
 __global__ void k_scale_c(int64_t M, int64_t N, double beta, double* __restrict__ C, int64_t ldc) {
     const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (idx >= M * N) return;
@@ -461,12 +506,27 @@ int dgemm_ozaki_blocks(dbcsr_matrix_s* A, bool ta, dbcsr_matrix_s* B, bool tb, d
                                   (size_t)s * N, st));
     }
     const int sgrid = ctx().num_sms * 16;
-    k_slice_blocks<<<(int)std::min<int64_t>(cdiv(A->nblks, 8), sgrid), 256, 0, st>>>(slice_geom(A, !ta), e.p, s,
-                                                                                     M, ldk, SA.p);
-    DB_KCHECK();
-    k_slice_blocks<<<(int)std::min<int64_t>(cdiv(B->nblks, 8), sgrid), 256, 0, st>>>(slice_geom(B, tb), f.p, s, N,
-                                                                                     ldk, SB.p);
-    DB_KCHECK();
+    // one block size per dimension: whole-line runs (k_slice_uniform); else block by block
+    auto uniform = [](const std::vector<int>& v) {
+        for (int x : v)
+            if (x != v[0]) return false;
+        return !v.empty();
+    };
+    auto slice = [&](dbcsr_matrix_s* X, bool x_is_row, int64_t lines, const int* ex, __nv_bfloat16* out) -> int {
+        if (uniform(X->h_rs) && uniform(X->h_cs)) {
+            const UniGeom G{X->d_data, x_is_row ? X->h_rs[0] : X->h_cs[0], x_is_row ? X->h_cs[0] : X->h_rs[0],
+                            (int64_t)X->nbc, x_is_row ? 1 : 0, lines, K};
+            const int64_t warps = lines * cdiv(K, 64);
+            k_slice_uniform<<<(int)std::min<int64_t>(cdiv(warps, 8), sgrid), 256, 0, st>>>(G, ex, s, ldk, out);
+        } else {
+            k_slice_blocks<<<(int)std::min<int64_t>(cdiv(X->nblks, 8), sgrid), 256, 0, st>>>(slice_geom(X, x_is_row),
+                                                                                          ex, s, lines, ldk, out);
+        }
+        DB_KCHECK();
+        return DBCSR_OK;
+    };
+    DB_TRY(slice(A, !ta, M, e.p, SA.p));
+    DB_TRY(slice(B, tb, N, f.p, SB.p));
     DBuf<int64_t> base;
     DBuf<int> stride;
     DB_TRY(base.alloc(M));
