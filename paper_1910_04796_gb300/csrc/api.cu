@@ -137,6 +137,18 @@ int download_index(dbcsr_matrix_s* m) {
     DB_TRY(d2h(m->h_col.data(), m->d_col, sizeof(int) * m->nblks));
     DB_TRY(d2h(m->h_off.data(), m->d_off, sizeof(int64_t) * (m->nblks + 1)));
     DB_TRY(sync_stream());
+    m->h_row_cs.assign(m->nbr, 0.0);
+    m->h_row_n.assign(m->nbr, 0);
+    m->h_col_rs.assign(m->nbc, 0.0);
+    m->h_col_n.assign(m->nbc, 0);
+    for (int i = 0; i < m->nbr; i++)
+        for (int q = m->h_rowptr[i]; q < m->h_rowptr[i + 1]; q++) {
+            const int j = m->h_col[q];
+            m->h_row_cs[i] += m->h_cs[j];
+            m->h_row_n[i]++;
+            m->h_col_rs[j] += m->h_rs[i];
+            m->h_col_n[j]++;
+        }
     m->h_valid = true;
     return DBCSR_OK;
 }
@@ -521,27 +533,15 @@ int check_conformant(bool ta, bool tb, dbcsr_matrix_s* A, dbcsr_matrix_s* B, dbc
 double useful_flops_host(bool ta, bool tb, dbcsr_matrix_s* A, dbcsr_matrix_s* B, int64_t* nprod) {
     // sum over k of (2 * k_size * sum_{i in col k of op A} m_i * sum_{j in row k of op B} n_j)
     // computed on the host from the downloaded indices
+    // (the per-line sums are kept with each matrix's host index: an operand
+    // that does not change costs one pass over its blocks, once)
     download_index(A);
     download_index(B);
     const int nk = ta ? A->nbr : A->nbc;
-    std::vector<double> am(nk, 0.0), bn(nk, 0.0);
-    std::vector<int64_t> ac(nk, 0), bc(nk, 0);
-    for (int i = 0; i < A->nbr; i++)
-        for (int q = A->h_rowptr[i]; q < A->h_rowptr[i + 1]; q++) {
-            int j = A->h_col[q];
-            int k = ta ? i : j;
-            int mm = ta ? A->h_cs[j] : A->h_rs[i];
-            am[k] += mm;
-            ac[k]++;
-        }
-    for (int i = 0; i < B->nbr; i++)
-        for (int q = B->h_rowptr[i]; q < B->h_rowptr[i + 1]; q++) {
-            int j = B->h_col[q];
-            int k = tb ? j : i;
-            int nn = tb ? B->h_rs[i] : B->h_cs[j];
-            bn[k] += nn;
-            bc[k]++;
-        }
+    const std::vector<double>& am = ta ? A->h_row_cs : A->h_col_rs;
+    const std::vector<int64_t>& ac = ta ? A->h_row_n : A->h_col_n;
+    const std::vector<double>& bn = tb ? B->h_col_rs : B->h_row_cs;
+    const std::vector<int64_t>& bc = tb ? B->h_col_n : B->h_row_n;
     double f = 0.0;
     int64_t np = 0;
     const std::vector<int>& ks = ta ? A->h_rs : A->h_cs;

@@ -133,6 +133,10 @@ struct dbcsr_matrix_s {
     bool h_valid = false;
     std::vector<int> h_rowptr, h_col;
     std::vector<int64_t> h_off;
+    // with the host index: per block row the sum of its blocks' column sizes and
+    // their count, per block column the sum of row sizes and the count
+    std::vector<double> h_row_cs, h_col_rs;
+    std::vector<int64_t> h_row_n, h_col_n;
     uint64_t version = 0;    // bumped whenever the pattern changes
     uint64_t uid = 0;
     void* plan = nullptr;    // reusable stack plan + CUDA graph (api.cu)

@@ -269,22 +269,54 @@ __global__ void __launch_bounds__(256, Q <= 16 ? 2 : 1) k_smm_fp32(SmmArgs g, co
 // lane j accumulates column j of the C block: per inner index l, one
 // conflict-free load of B(l, j) and broadcast 16-byte loads of A(:, l) feed
 // m FMAs. FMA order per element: products in plan order, l ascending.
-// Rows m..m+3 of a partial float4 read stale values into accumulators that
+// Two staging buffers per warp: the asynchronous copies (cp.async, 4 bytes
+// each) of the next product's blocks run while the current one is computed.
+// Rows m..m+3 of a partial float4 read values that feed accumulators which
 // are never stored.
-constexpr int F32_WARPS = 8;
+constexpr int F32_WARPS = 4;
 constexpr int F32_BSTRIDE = 33;   // sB[j * 33 + l]: lanes j read distinct banks
 constexpr int F32_ASTRIDE = 36;   // sA[l * 36 + i]: 16-byte aligned columns, transposed writes 4-way at most
 
-constexpr int F32_WARP_FLOATS = 32 * F32_ASTRIDE + 32 * F32_BSTRIDE + 32;   // A, B (+ pad to 16 bytes)
+constexpr int F32_BUF_FLOATS = 32 * F32_ASTRIDE + 32 * F32_BSTRIDE + 32;   // A, B (+ pad to 16 bytes)
+constexpr int F32_WARP_FLOATS = 2 * F32_BUF_FLOATS;
 constexpr int F32_SMEM = F32_WARPS * F32_WARP_FLOATS * (int)sizeof(float);
+
+__device__ __forceinline__ void cp_async4(float* dst, const float* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+
+// the copies of one product's op(A) (m x kk) and op(B) (kk x n) blocks into a
+// staging buffer; the lane runs along the contiguous index of each stored block
+template <int TA, int TB>
+__device__ __forceinline__ void f32_stage(const float* ga, const float* gb, int m, int n, int kk, float* a_s,
+                                          float* b_s, int lane) {
+    // op(A): element (i, l) of the stored block at i + l*m (TA = 0) or l + i*kk (TA = 1)
+    if (!TA) {
+        if (lane < m)
+            for (int l = 0; l < kk; l++) cp_async4(a_s + l * F32_ASTRIDE + lane, ga + lane + l * m);
+    } else {
+        if (lane < kk)
+            for (int i = 0; i < m; i++) cp_async4(a_s + lane * F32_ASTRIDE + i, ga + lane + i * kk);
+    }
+    // op(B): element (l, j) at l + j*kk (TB = 0) or j + l*n (TB = 1)
+    if (!TB) {
+        if (lane < kk)
+            for (int j = 0; j < n; j++) cp_async4(b_s + j * F32_BSTRIDE + lane, gb + lane + j * kk);
+    } else {
+        if (lane < n)
+            for (int l = 0; l < kk; l++) cp_async4(b_s + lane * F32_BSTRIDE + l, gb + lane + l * n);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
 
 template <int TA, int TB>
 __global__ void __launch_bounds__(32 * F32_WARPS) k_smm_f32_tile(SmmArgs g, int chunk) {
     extern __shared__ __align__(16) float f32_smem[];
     __shared__ int s_cb[F32_WARPS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float* a_s = f32_smem + warp * F32_WARP_FLOATS;   // A(i, l) at l * 36 + i
-    float* b_s = a_s + 32 * F32_ASTRIDE;               // B(l, j) at j * 33 + l
+    float* wbuf = f32_smem + warp * F32_WARP_FLOATS;   // per buffer: A(i, l) at l * 36 + i, then B(l, j) at j * 33 + l
     const BlasUpd bu(g.alpha, g.beta);
     for (;;) {
         if (lane == 0) s_cb[warp] = (int)atomicAdd(g.counter, (unsigned long long)chunk);
@@ -299,34 +331,37 @@ __global__ void __launch_bounds__(32 * F32_WARPS) k_smm_f32_tile(SmmArgs g, int 
             float acc[32];
 #pragma unroll
             for (int i = 0; i < 32; i++) acc[i] = 0.f;
-            for (int64_t p = p0; p < p1; p++) {
+            // operands of product p: offsets and inner size
+            auto operands = [&](int64_t p, const float*& ga, const float*& gb, int& kk) {
                 const int2 pr = g.prod[p];
                 const int64_t ao = g.A.off[pr.x], bo = g.B.off[pr.y];
-                const int kk = (int)(g.A.off[pr.x + 1] - ao) / m;
-                const float* ga = g.A32 + ao;
-                const float* gb = g.B32 + bo;
-                __syncwarp();   // the previous product's operands are consumed
-                // op(A) is m x kk: element (i, l) of the stored block is at
-                // i + l*m (TA = 0) or l + i*kk (TA = 1); the lane runs along the
-                // contiguous index, so the reads are coalesced
-                if (!TA) {
-                    if (lane < m)
-                        for (int l = 0; l < kk; l++) a_s[l * F32_ASTRIDE + lane] = ga[lane + l * m];
+                kk = (int)(g.A.off[pr.x + 1] - ao) / m;
+                ga = g.A32 + ao;
+                gb = g.B32 + bo;
+            };
+            const float *ga = nullptr, *gb = nullptr;
+            int kk = 0;
+            if (p0 < p1) {
+                operands(p0, ga, gb, kk);
+                f32_stage<TA, TB>(ga, gb, m, n, kk, wbuf, wbuf + 32 * F32_ASTRIDE, lane);
+            }
+            for (int64_t p = p0; p < p1; p++) {
+                const int cur_kk = kk;
+                float* a_s = wbuf + ((p - p0) & 1) * F32_BUF_FLOATS;
+                float* b_s = a_s + 32 * F32_ASTRIDE;
+                if (p + 1 < p1) {
+                    // the other buffer was last read by product p - 1, finished by every lane
+                    __syncwarp();
+                    operands(p + 1, ga, gb, kk);
+                    float* na = wbuf + ((p + 1 - p0) & 1) * F32_BUF_FLOATS;
+                    f32_stage<TA, TB>(ga, gb, m, n, kk, na, na + 32 * F32_ASTRIDE, lane);
+                    asm volatile("cp.async.wait_group 1;" ::: "memory");
                 } else {
-                    if (lane < kk)
-                        for (int i = 0; i < m; i++) a_s[lane * F32_ASTRIDE + i] = ga[lane + i * kk];
+                    asm volatile("cp.async.wait_group 0;" ::: "memory");
                 }
-                // op(B) is kk x n: element (l, j) at l + j*kk (TB = 0) or j + l*n (TB = 1)
-                if (!TB) {
-                    if (lane < kk)
-                        for (int j = 0; j < n; j++) b_s[j * F32_BSTRIDE + lane] = gb[lane + j * kk];
-                } else {
-                    if (lane < n)
-                        for (int l = 0; l < kk; l++) b_s[lane * F32_BSTRIDE + l] = gb[lane + l * n];
-                }
-                __syncwarp();
+                __syncwarp();   // product p's blocks are in shared memory for every lane
                 if (lane < n) {
-                    for (int l = 0; l < kk; l++) {
+                    for (int l = 0; l < cur_kk; l++) {
                         const float b = b_s[lane * F32_BSTRIDE + l];
                         const float4* ac = reinterpret_cast<const float4*>(a_s + l * F32_ASTRIDE);
 #pragma unroll
@@ -342,6 +377,7 @@ __global__ void __launch_bounds__(32 * F32_WARPS) k_smm_f32_tile(SmmArgs g, int 
                     }
                 }
             }
+            __syncwarp();   // the next C block's first copies overwrite buffer 0
             // column j = lane of the C block; alpha / beta in FP64
             if (lane < n) {
                 double* cout = g.Cd + g.c_off[cb] + (int64_t)lane * m;
