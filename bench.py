@@ -386,6 +386,40 @@ def main():
                 "traffic": dram_traffic(w.name, precision, path_taken), "kernel_ms": main_ms,
                 "algorithmic_flops": s2["main_flops"], "peak_source": peak_note}
 
+    # end to end through the C ABI with host buffers (H2D of inputs and D2H of C inside);
+    # measured before the comparison legs, which leave large allocations and a hot GPU behind
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+        hA, hB = pin(w.A.data), pin(w.B.data)
+        hC = pin(C0.data) if C0 is not None else None
+        # the result is read into pinned host memory too (allocated once, like the inputs)
+        hOut = pin(np.zeros(max(1, int(Cm.info()[3])), np.float64))
+        out = None
+
+        def e2e_step():
+            nonlocal out
+            Ah = dbcsr.Matrix.create(w.A.row_sizes, w.A.col_sizes, w.A.blk_row, w.A.blk_col, hA)
+            Bh = dbcsr.Matrix.create(w.B.row_sizes, w.B.col_sizes, w.B.blk_row, w.B.blk_col, hB)
+            if C0 is not None:
+                Ch = dbcsr.Matrix.create(C0.row_sizes, C0.col_sizes, C0.blk_row, C0.blk_col, hC)
+            else:
+                Ch = dbcsr.Matrix.create(rs, cs, np.zeros(0, np.int32), np.zeros(0, np.int32))
+            dbcsr.multiply(w.transa, w.transb, w.alpha, Ah, Bh, w.beta, Ch, path=args.path, precision=precision,
+                           ozaki_slices=args.slices, kernel=args.kernel, hybrid_panel=hpanel,
+                           hybrid_fill_pct=args.hybrid_fill)
+            out = Ch.data(hOut)
+            for m in (Ah, Bh, Ch):
+                m.release()
+
+        e2e_steps = max(1, min(args.steps, 3))
+        s_e2e, _ = time_steps(e2e_step, e2e_steps, 2, world)
+        s_e2e = max_over_ranks(s_e2e, world)
+        h2d = (hA.nbytes + hB.nbytes + (hC.nbytes if hC is not None else 0)
+               + 4 * 2 * (w.A.nblks + w.B.nblks + (C0.nblks if C0 is not None else 0)))
+        e2e = {"value": useful * world * e2e_steps / s_e2e / 1e12, "unit": "TFLOP/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(out.nbytes if out is not None else 0)}
+
     # comparison legs on the same GPU and inputs: the plain FP64 paths, the
     # emulated and TF32 paths with their error against the GPU FP64 result
     legs, accuracy = {}, {}
@@ -422,39 +456,6 @@ def main():
             legs["fp64_stacks_graph_replay"] = useful * 50 / s_rep / 1e12
             legs["graph_replay_us_per_multiply"] = s_rep / 50 * 1e6
             Cl.release()
-
-    # end to end through the C ABI with host buffers (H2D of inputs and D2H of C inside)
-    e2e = None
-    if not args.no_e2e:
-        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
-        hA, hB = pin(w.A.data), pin(w.B.data)
-        hC = pin(C0.data) if C0 is not None else None
-        # the result is read into pinned host memory too (allocated once, like the inputs)
-        hOut = pin(np.zeros(max(1, int(Cm.info()[3])), np.float64))
-        out = None
-
-        def e2e_step():
-            nonlocal out
-            Ah = dbcsr.Matrix.create(w.A.row_sizes, w.A.col_sizes, w.A.blk_row, w.A.blk_col, hA)
-            Bh = dbcsr.Matrix.create(w.B.row_sizes, w.B.col_sizes, w.B.blk_row, w.B.blk_col, hB)
-            if C0 is not None:
-                Ch = dbcsr.Matrix.create(C0.row_sizes, C0.col_sizes, C0.blk_row, C0.blk_col, hC)
-            else:
-                Ch = dbcsr.Matrix.create(rs, cs, np.zeros(0, np.int32), np.zeros(0, np.int32))
-            dbcsr.multiply(w.transa, w.transb, w.alpha, Ah, Bh, w.beta, Ch, path=args.path, precision=precision,
-                           ozaki_slices=args.slices, kernel=args.kernel, hybrid_panel=hpanel,
-                           hybrid_fill_pct=args.hybrid_fill)
-            out = Ch.data(hOut)
-            for m in (Ah, Bh, Ch):
-                m.release()
-
-        e2e_steps = max(1, min(args.steps, 3))
-        s_e2e, _ = time_steps(e2e_step, e2e_steps, 1, world)
-        s_e2e = max_over_ranks(s_e2e, world)
-        h2d = (hA.nbytes + hB.nbytes + (hC.nbytes if hC is not None else 0)
-               + 4 * 2 * (w.A.nblks + w.B.nblks + (C0.nblks if C0 is not None else 0)))
-        e2e = {"value": useful * world * e2e_steps / s_e2e / 1e12, "unit": "TFLOP/s",
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(out.nbytes if out is not None else 0)}
 
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:

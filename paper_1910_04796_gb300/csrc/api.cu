@@ -285,18 +285,21 @@ int dbcsr_create(dbcsr_matrix* out, int nbr, int nbc, const int* rs, const int* 
         if (rs[i] < 1) return fail(DBCSR_ERR_ARG, "create: row block size < 1 at " + std::to_string(i));
     for (int j = 0; j < nbc; j++)
         if (cs[j] < 1) return fail(DBCSR_ERR_ARG, "create: col block size < 1 at " + std::to_string(j));
-    for (int64_t b = 0; b < nblks; b++)
+    // coordinates in range, and whether the blocks already come in CSR order
+    // (row, then column, no duplicates) -- one pass
+    bool sorted = true;
+    for (int64_t b = 0; b < nblks; b++) {
         if (br[b] < 0 || br[b] >= nbr || bc[b] < 0 || bc[b] >= nbc)
             return fail(DBCSR_ERR_ARG, "create: block coordinate out of range at " + std::to_string(b));
+        if (b > 0 && (br[b] < br[b - 1] || (br[b] == br[b - 1] && bc[b] <= bc[b - 1]))) sorted = false;
+    }
     DB_TRY(ensure_device());
 
     // CSR order of the blocks (row, then column), duplicates rejected
-    std::vector<int64_t> perm(nblks);
-    std::iota(perm.begin(), perm.end(), 0);
-    bool sorted = true;
-    for (int64_t b = 1; b < nblks && sorted; b++)
-        if (br[b] < br[b - 1] || (br[b] == br[b - 1] && bc[b] <= bc[b - 1])) sorted = false;
+    std::vector<int64_t> perm;
     if (!sorted) {
+        perm.resize(nblks);
+        std::iota(perm.begin(), perm.end(), 0);
         std::stable_sort(perm.begin(), perm.end(), [&](int64_t x, int64_t y) {
             return br[x] != br[y] ? br[x] < br[y] : bc[x] < bc[y];
         });
@@ -313,7 +316,7 @@ int dbcsr_create(dbcsr_matrix* out, int nbr, int nbc, const int* rs, const int* 
     std::vector<int> rowptr(nbr + 1, 0), col(nblks), row_of(nblks);
     std::vector<int64_t> off(nblks + 1, 0), src_off;
     for (int64_t q = 0; q < nblks; q++) {
-        int64_t b = perm[q];
+        const int64_t b = sorted ? q : perm[q];
         rowptr[br[b] + 1]++;
         col[q] = bc[b];
         row_of[q] = br[b];

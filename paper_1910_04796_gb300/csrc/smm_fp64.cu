@@ -6,14 +6,16 @@
 // GB300 kernels that play that role for FP64, and the per-shape dispatch that
 // the autotuner's table drives.
 //
-// GB300 facts that shape them: FP64 runs at about 1 TFLOP/s on the whole chip
-// (DFMA and DMMA alike), i.e. under two FP64 FMAs per clock per SM, so a block
-// product is arithmetic-bound once its operands are on chip (the ridge point
-// is ~0.15 flop/byte against 6.7 TB/s HBM). What matters is (1) keeping every
-// lane of every DFMA busy (elements mapped densely onto lanes), (2) enough
-// independent accumulators and resident warps to cover latency, (3) never
-// waiting on a chain of dependent index loads per product, (4) reading each C
-// block once and writing it once.
+// GB300 facts that shape them: the FP64 pipe does two FMAs per clock per SM
+// (1.26 TFLOP/s at 2 070 MHz; the FP64 MMA is no faster), so a block product
+// is arithmetic-bound once its operands are on chip (the ridge point is ~0.2
+// flop/byte against 6.7 TB/s HBM). What matters is (1) keeping every lane of
+// every DFMA busy (elements mapped densely onto lanes) -- and issuing no DFMA
+// for idle lanes: one under a false predicate still takes its pipe cycles --
+// (2) enough independent accumulators and resident warps to cover latency,
+// (3) never waiting on a chain of dependent index loads per product, and
+// operands in L1 before they are used, (4) reading each C block once and
+// writing it once.
 //
 // A team of W warps owns one C block: it walks the block's products (ascending
 // k, as stack generation ordered them; with W > 1 warp w takes products w,
