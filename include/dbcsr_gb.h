@@ -97,7 +97,7 @@ typedef struct {
                           2: two warps per C block (products split);
                           3: four warps per C block.
                           Every C block of a multiply runs in one launch.
-                          Emulated-FP64 stack kernel: 0 = tcgen05 when every
+                          Emulated-FP64 stack kernel: 0 = tcgen05 when the mean
                           block edge is at least 12, else mma.sync; 1 = mma.sync
                           (blocks padded to 16); 2 = tcgen05 (blocks padded to
                           32 x 32, fp32 accumulators in tensor memory)      */

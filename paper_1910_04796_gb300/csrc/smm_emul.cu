@@ -394,16 +394,20 @@ int smm_emulated(const SmmArgs& g, dbcsr_matrix_s* A, bool ta, dbcsr_matrix_s* B
     DBuf<int> e, f;
     DB_TRY(line_exponents(A, !ta, Mop, e));
     DB_TRY(line_exponents(B, tb, Nop, f));
-    // kernel: 0 = tcgen05 when every block edge is at least 12, else mma.sync;
-    // 1 = mma.sync; 2 = tcgen05. Measured on GB300: 22 x 22 blocks padded to
-    // 32 x 32 run 5.8x faster on tcgen05; mixed 5..32 blocks slightly faster
-    // on mma.sync (padding to 16 instead of 32)
-    int kmin = 1 << 30;
-    for (const std::vector<int>* v : {&A->h_rs, &A->h_cs, &B->h_rs, &B->h_cs})
-        for (int x : *v) kmin = std::min(kmin, x);
+    // kernel: 0 = tcgen05 when the mean block edge is at least 12, else
+    // mma.sync; 1 = mma.sync; 2 = tcgen05. Measured on GB300: 22 x 22 blocks
+    // padded to 32 x 32 run 5.8x faster on tcgen05, the mixed 5..32 blocks of
+    // the uneven workload (mean edge 17.9) 1.18x faster; the mma.sync kernel
+    // pads to 16 instead of 32, which pays only for small blocks
+    double esum = 0.0;
+    int64_t ecount = 0;
+    for (const std::vector<int>* v : {&A->h_rs, &A->h_cs, &B->h_rs, &B->h_cs}) {
+        for (int x : *v) esum += x;
+        ecount += (int64_t)v->size();
+    }
     const bool tc_ok = smm_emul_tc_usable();
     if (o.kernel == 2 && !tc_ok) return fail(DBCSR_ERR_STATE, "tcgen05 emulated stack kernel unavailable");
-    if (o.kernel == 2 || (o.kernel == 0 && kmin >= 12 && tc_ok))
+    if (o.kernel == 2 || (o.kernel == 0 && ecount > 0 && esum >= 12.0 * (double)ecount && tc_ok))
         return smm_emul_tc(g, A, ta, B, tb, C, e.p, f.p, s, nprod, main_flops, ranges);
     DBuf<int64_t> soffA, soffB;
     DBuf<__nv_bfloat16> SA, SB;
