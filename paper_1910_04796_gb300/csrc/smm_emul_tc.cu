@@ -14,33 +14,37 @@
 // operand layout of tcgen05: 8-row x 16-byte core matrices, core (r/8, k/8)
 // at byte ((r/8) * 4 + k/8) * 128 of the slice (leading-dimension byte offset
 // 128 between K neighbours, stride byte offset 512 between 8-row groups).
-// Consecutive slices therefore form one taller operand, and one bulk copy
-// brings all s slices of a block into shared memory. Per product two MMA
-// groups, each K = 32 (two K = 16 instructions):
-//   G1: rows A slices 1..4 (M = 128) x columns B slices 1..s (N = 32 s)
-//   G2: rows A slices s, s-1, .., 5 (M = 128, padded) x columns B slices
-//       1..s-4 (N = 32 (s-4)); A's slices are stored in the order
-//       1, 2, 3, 4, s, s-1, .., 5 so that G2 is one operand and every lane
-//       quadrant q holds the slices q + 1 and s - q, which balances the
-//       epilogue's work over the quadrants
-// so pair (t, u) owns a 32 x 32 accumulator block of TMEM (lane quadrant
-// t - 1 or s - t, columns 32 (u-1), + 32 s for G2); pairs with t + u > s + 1
-// are computed and ignored. A C block's products run in chunks of 16: an fp32
-// accumulator then stays below 2^23 (16 * 32 * 127^2), so the G1 and G2 sums
-// of a level are added exactly in fp32 before one conversion to int32.
+// Consecutive slices therefore form one taller operand.
+//
+// One accumulator of M = 128 rows x N = 32 s columns per C block: lane
+// quadrant q, column group u is slot (q, u). Per product, up to three operand
+// segments of K = 32 (two K = 16 instructions each) accumulate into it:
+//   segment 0: A slices 1, 2, 3, 4 as the quadrants x B slices 1..s
+//   segment 1: A slices 0, 5, 6, 7 (0: zero slice) x B slices 0, 0, 0, 1, 2, ..
+//   segment 2: A slices 0, 0, 0, 8                 x B slices 0, 0, 0, 0, 1, ..
+// so slot (q, u) sums the pairs (q+1, u), (q+4, u-3) and (8, u-4) where they
+// exist -- all of level q + 1 + u. Every pair t + u <= s + 1 lands in exactly
+// one slot with u <= s - q, and each such slot holds one level. The slots fit
+// in 256 TMEM columns, so the accumulator is double-buffered: the MMAs of the
+// next chunk of products run while the previous chunk is drained. In shared
+// memory A's slots are [1 2 3 4 | 0 5 6 7 | 0 0 0 8] and B's [0 0 0 (0) 1 .. s]
+// (zero slices written once), so every segment's operand is one contiguous
+// window. A C block's products run in chunks of 16 (10 with three segments):
+// a slot then stays below 2^24 and converts to int32 exactly.
 //
 // Warps: 0 bulk-copy producer (one lane), 1 TMEM owner and MMA issuer (one
-// lane), 2-9 epilogue; epilogue warp w reads TMEM lane quadrant q = w % 4,
-// i.e. A slice t = q + 1 of G1 and t = s - q of G2, two warps per quadrant
-// splitting the columns. Every role reads its C blocks from a schedule in
-// traversal order (product range, offsets, sizes in one record) and loads
-// the next record ahead. Per chunk the epilogue
-//   1. drains TMEM: level d's contribution of its slices, P_{t,d-t} (+ the
-//      G2 term), converted exactly to int32, into a level block in shared
-//      memory; then releases TMEM, so the next chunk's MMAs overlap the rest;
-//   2. sums the level blocks of the four quadrants into per-thread int32
-//      level sums (thread: row i = lane, four columns).
-// After the C block's last chunk it recombines, rounds, scales and stores.
+// lane), 2-5 drain, 6-13 finish. Every role reads its C blocks from a schedule
+// in traversal order (product range, offsets, sizes in one record) and loads
+// the next record ahead.
+//   drain warp q (TMEM lane quadrant q = warp % 4, row i = lane): per chunk,
+//     reads the slots (q, u), u = 1 .. s - q (all 32 columns), converts each
+//     once to int32 and adds it into level q + 1 + u of the C block's level
+//     sums in shared memory (int32 atomics: the four quadrants contribute to
+//     the same levels); then releases the TMEM buffer.
+//   finish warps: once a C block's level sums are complete, each thread (row
+//     i = lane, four columns) reads and zeroes its level sums, hands the buffer
+//     back, recombines exactly, rounds, scales and stores -- while the drain
+//     warps fill the other of the two level-sum buffers with the next C block.
 // int32 level sums are exact while products * s * 32 * 127^2 < 2^31 (checked
 // on the host). Every wait is bounded (4 s): on expiry the kernel sets the
 // error flag, the other roles see the abort flag, every role leaves its loop
@@ -56,44 +60,53 @@ namespace dbcsr {
 
 namespace {
 
-constexpr int TC_R = 2;                       // epilogue warps per TMEM lane quadrant
-constexpr int TC_EPI = 4 * TC_R;              // epilogue warps
-constexpr int TC_THREADS = 64 + 32 * TC_EPI;  // producer warp, MMA warp, epilogue
-constexpr int TC_COLS = 32 / TC_R;            // accumulator columns an epilogue warp drains per block
-constexpr int TC_EL = 8 / TC_R;               // C elements per epilogue thread
+constexpr int TC_DRAIN = 4;                   // drain warps: one per TMEM lane quadrant
+constexpr int TC_FIN = 8;                     // finish warps
+constexpr int TC_THREADS = 64 + 32 * (TC_DRAIN + TC_FIN);   // producer warp, MMA warp, drain, finish
+constexpr int TC_EL = 32 / TC_FIN;            // C elements (columns of a row) per finish thread
+constexpr int TC_LROW = 33;                   // level-sum row stride in words: rows and columns conflict-free
 constexpr int TC_SLOT = 2048;                 // one 32 x 32 bf16 slice
 constexpr int TC_SMEM_CAP = 232448;           // 227 KB of shared memory per CTA
 constexpr int TC_SMEM_MIN = 120 * 1024;       // one CTA per SM: it allocates all 512 TMEM columns
-constexpr int TC_CHUNK = 16;                  // products per exact fp32 stretch (16 * 32 * 127^2 < 2^23)
+constexpr int TC_ACC_COLS = 256;              // TMEM columns of one accumulator buffer (two buffers)
 constexpr uint64_t TC_WAIT_NS = 4000000000ull;
 // C blocks are visited tile by tile: the CTAs working at the same time share
 // the tile's A block rows and B block columns, which stay in L2
 constexpr int TC_TILE = 32;
 
+// Operand segments. Quadrant q of the M = 128 accumulator rows holds one A
+// slice, column group u (32 columns) one B slice; every pair (t, u) that a
+// level t + u <= s + 1 needs lands in a slot whose first pair has the same
+// level, so each slot's fp32 sum belongs to one level:
+//   segment 0: A slices 1, 2, 3, 4      x B slices u           (pairs (q+1, u))
+//   segment 1: A slices -, 5, 6, 7      x B slices u - 3, u>=4 (pairs (q+4, u-3))
+//   segment 2: A slices -, -, -, 8      x B slices u - 4, u>=5 (pairs (8, u-4))
+// ("-": zero slice). In shared memory A's slots are [1 2 3 4 | 0 5 6 7 | 0 0 0 8]
+// and B's [0 0 0 0 | 1 .. s] (zero prefix 3 for two segments), so each
+// segment's operand is one contiguous window.
 template <int S>
 struct TcGeo {
-    static constexpr int STAGE = 2 * S * TC_SLOT;                 // A then B slices of one product
-    static constexpr int T1 = S < 4 ? S : 4;                      // A slices of G1 that exist
-    static constexpr int N1 = 32 * S;
-    static constexpr int N2 = S > 4 ? 32 * (S - 4) : 0;
-    static constexpr int NBLK = T1 * S - T1 * (T1 - 1) / 2;       // level blocks of the staging area
-    static constexpr int STG = NBLK * 4096;                       // 32 x 32 int32 each
+    static constexpr int NSEG = S <= 4 ? 1 : (S <= 7 ? 2 : 3);
+    static constexpr int A_SLOTS = 4 * NSEG;
+    static constexpr int B_ZERO = NSEG == 1 ? 0 : (NSEG == 2 ? 3 : 4);
+    static constexpr int B_SLOTS = B_ZERO + S;
+    static constexpr int STAGE = (A_SLOTS + B_SLOTS) * TC_SLOT;
+    static constexpr int N = 32 * S;                              // accumulator columns
+    // products per exact fp32 stretch: a slot sums up to NSEG pairs of
+    // CHUNK * 32 * 127^2 each, below 2^24
+    static constexpr int CHUNK = NSEG <= 2 ? 16 : 10;
+    static constexpr int LSBUF = S * 32 * TC_LROW;                // int32 level sums of one C block
+    static constexpr int LS = 2 * LSBUF * 4;                      // two buffers, bytes
     static constexpr int RESERVE = 1024 + 256;                    // alignment + barriers
-    static constexpr int NST0 = (TC_SMEM_CAP - RESERVE - STG) / STAGE;
+    static constexpr int NST0 = (TC_SMEM_CAP - RESERVE - LS) / STAGE;
     static constexpr int NST = NST0 > 6 ? 6 : NST0;
-    static constexpr int SMEM0 = NST * STAGE + STG + RESERVE;
+    static constexpr int SMEM0 = NST * STAGE + LS + RESERVE;
     static constexpr int SMEM = SMEM0 < TC_SMEM_MIN ? TC_SMEM_MIN : SMEM0;
-    static constexpr uint32_t IDESC1 = ptx::idesc_f32acc(1, 128, N1);
-    static constexpr uint32_t IDESC2 = ptx::idesc_f32acc(1, 128, N2 > 0 ? N2 : 32);
-    static_assert(N1 + N2 <= 512, "accumulators exceed TMEM");
+    static constexpr uint32_t IDESC = ptx::idesc_f32acc(1, 128, N);
+    static_assert(N <= TC_ACC_COLS, "accumulator exceeds its TMEM buffer");
+    static_assert(NSEG * CHUNK * 32 * 127 * 127 < (1 << 24), "fp32 stretch not exact");
     static_assert(NST >= 2, "at least two pipeline stages");
 };
-
-// staging block of quadrant w (A slice w + 1) for level d, w + 2 <= d <= S + 1
-template <int S>
-__host__ __device__ constexpr int lvl_blk(int w, int d) {
-    return w * S - w * (w - 1) / 2 + (d - w - 2);
-}
 
 // One C block in traversal order: everything the three roles need, one record.
 struct __align__(16) TcBlk {
@@ -121,8 +134,8 @@ struct TcArgs {
 };
 
 // Slices of every stored block in the operand layout above, zero-padded to
-// 32 x 32: warp per block, lane per 8-element chunk of a row.
-// A (is_a) stores slice t in slot t - 1 for t <= 4 and 4 + s - t above; B in slot t - 1.
+// 32 x 32: warp per block, lane per 8-element chunk of a row; slice t in slot
+// t - 1 (is_a is kept for the call sites: both operands use the same order).
 __global__ void k_tc_slice(SliceGeom G, const int* __restrict__ ex, int s, int is_a, uint8_t* __restrict__ out) {
     const int lane = threadIdx.x & 31;
     const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -151,7 +164,7 @@ __global__ void k_tc_slice(SliceGeom G, const int* __restrict__ ex, int s, int i
                                                                  emul::slice_bf16(q[2 * k + 1], t, s));
                     w[k] = *reinterpret_cast<const uint32_t*>(&pr);
                 }
-                const int slot = (is_a && t > 4) ? 4 + s - t : t - 1;
+                const int slot = t - 1;
                 *reinterpret_cast<uint4*>(o + slot * 1024 + pos) = make_uint4(w[0], w[1], w[2], w[3]);
             }
         }
@@ -211,14 +224,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_smm_emul_tc(TcArgs a) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* stages = smem;
-    uint8_t* stg = smem + G::NST * G::STAGE;
-    uint64_t* full = reinterpret_cast<uint64_t*>(stg + G::STG);
+    int* LS = reinterpret_cast<int*>(smem + G::NST * G::STAGE);   // [2][S][32][TC_LROW] level sums
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + G::NST * G::STAGE + G::LS);
     uint64_t* empty = full + G::NST;
-    uint64_t* tfull = empty + G::NST;   // MMA -> epilogue: a chunk's pair sums are in TMEM
-    uint64_t* tempty = tfull + 1;       // epilogue -> MMA: TMEM drained
-    uint64_t* sfull = tempty + 1;       // staging area written by all epilogue threads
-    uint64_t* sfree = sfull + 1;        // staging area read by all epilogue threads
-    uint64_t* drain = sfree + 1;
+    uint64_t* tfull = empty + G::NST;   // [2] MMA -> drain: a chunk's sums are in TMEM buffer b
+    uint64_t* tempty = tfull + 2;       // [2] drain -> MMA: TMEM buffer b drained
+    uint64_t* lfull = tempty + 2;       // [2] drain -> finish: a C block's level sums are complete
+    uint64_t* lfree = lfull + 2;        // [2] finish -> drain: level sums read and zeroed
+    uint64_t* drain = lfree + 2;
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(drain + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
 
@@ -228,14 +241,22 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_smm_emul_tc(TcArgs a) {
             ptx::mbar_init(&full[i], 1);
             ptx::mbar_init(&empty[i], 1);
         }
-        ptx::mbar_init(tfull, 1);
-        ptx::mbar_init(tempty, 32 * TC_EPI);
-        ptx::mbar_init(sfull, 32 * TC_EPI);
-        ptx::mbar_init(sfree, 32 * TC_EPI);
+        for (int b = 0; b < 2; b++) {
+            ptx::mbar_init(&tfull[b], 1);
+            ptx::mbar_init(&tempty[b], 32 * TC_DRAIN);
+            ptx::mbar_init(&lfull[b], 32 * TC_DRAIN);
+            ptx::mbar_init(&lfree[b], 32 * TC_FIN);
+        }
         ptx::mbar_init(drain, 1);
         *abort_flag = 0;
         ptx::fence_mbar_init();
     }
+    // zero slices of the operand windows (never written by the copies) and
+    // level sums; the tensor cores read the stages through the async proxy
+    for (int w = threadIdx.x; w < G::NST * G::STAGE / 16; w += blockDim.x)
+        reinterpret_cast<uint4*>(stages)[w] = make_uint4(0u, 0u, 0u, 0u);
+    for (int w = threadIdx.x; w < 2 * G::LSBUF; w += blockDim.x) LS[w] = 0;
+    ptx::fence_proxy_async_shared();
     if (warp == 1) {
         ptx::tmem_alloc(tmem_holder, 512);
         ptx::tmem_relinquish();
@@ -252,6 +273,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_smm_emul_tc(TcArgs a) {
     if (warp == 0) {
         if (lane == 0) {
             // ------------------------------------------------ bulk-copy producer
+            // a product's slices: A 1..4 to slots 0.., A 5..7 to slots 5.., A 8 to
+            // slot 11; B 1..s to slots B_ZERO..
             int64_t it = 0;
             bool ok = true;
             longlong2 nxt = sched_range(a, blockIdx.x);
@@ -268,9 +291,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_smm_emul_tc(TcArgs a) {
                         break;
                     }
                     uint8_t* sa = stages + st * G::STAGE;
-                    ptx::mbar_arrive_expect_tx(&full[st], G::STAGE);
-                    ptx::bulk_load(sa, a.SA + (int64_t)pr.x * (S * TC_SLOT), S * TC_SLOT, &full[st]);
-                    ptx::bulk_load(sa + S * TC_SLOT, a.SB + (int64_t)pr.y * (S * TC_SLOT), S * TC_SLOT, &full[st]);
+                    uint8_t* sb = sa + G::A_SLOTS * TC_SLOT;
+                    const uint8_t* ga = a.SA + (int64_t)pr.x * (S * TC_SLOT);
+                    ptx::mbar_arrive_expect_tx(&full[st], 2 * S * TC_SLOT);
+                    ptx::bulk_load(sa, ga, (S < 4 ? S : 4) * TC_SLOT, &full[st]);
+                    if (S > 4) ptx::bulk_load(sa + 5 * TC_SLOT, ga + 4 * TC_SLOT, ((S < 7 ? S : 7) - 4) * TC_SLOT, &full[st]);
+                    if (S > 7) ptx::bulk_load(sa + 11 * TC_SLOT, ga + 7 * TC_SLOT, TC_SLOT, &full[st]);
+                    ptx::bulk_load(sb + G::B_ZERO * TC_SLOT, a.SB + (int64_t)pr.y * (S * TC_SLOT), S * TC_SLOT,
+                                   &full[st]);
                 }
             }
             // no copy may still be in flight when the CTA exits
@@ -284,20 +312,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_smm_emul_tc(TcArgs a) {
     } else if (warp == 1) {
         if (lane == 0) {
             // ------------------------------------------------------ MMA issuer
+            // chunk ci accumulates into TMEM buffer ci % 2 (columns 256 (ci % 2) ..)
             int64_t it = 0, ci = 0;
             bool ok = true;
             longlong2 nxt = sched_range(a, blockIdx.x);
             for (int64_t seq = blockIdx.x; seq < a.nC && ok; seq += gridDim.x) {
                 const longlong2 cur = nxt;
                 nxt = sched_range(a, seq + gridDim.x);
-                for (int64_t c0 = cur.x; c0 < cur.y && ok; c0 += TC_CHUNK, ci++) {
-                    if (*abort_flag || !ptx::mbar_wait_bounded(tempty, (uint32_t)((ci & 1) ^ 1), TC_WAIT_NS)) {
+                for (int64_t c0 = cur.x; c0 < cur.y && ok; c0 += G::CHUNK, ci++) {
+                    const int tb = (int)(ci & 1);
+                    if (*abort_flag ||
+                        !ptx::mbar_wait_bounded(&tempty[tb], (uint32_t)(((ci >> 1) & 1) ^ 1), TC_WAIT_NS)) {
                         if (!*abort_flag) on_timeout();
                         ok = false;
                         break;
                     }
                     ptx::tc_fence_after();
-                    const int64_t c1 = c0 + TC_CHUNK < cur.y ? c0 + TC_CHUNK : cur.y;
+                    const uint32_t d = tmem + (uint32_t)(tb * TC_ACC_COLS);
+                    const int64_t c1 = c0 + G::CHUNK < cur.y ? c0 + G::CHUNK : cur.y;
                     for (int64_t p = c0; p < c1; p++, it++) {
                         const int st = (int)(it % G::NST);
                         const uint32_t ph = (uint32_t)((it / G::NST) & 1);
@@ -308,135 +340,118 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_smm_emul_tc(TcArgs a) {
                         }
                         ptx::tc_fence_after();
                         const uint8_t* sa = stages + st * G::STAGE;
-                        const uint64_t a1 = ptx::smem_desc_kmajor(sa, 128, 512);
-                        const uint64_t a2 = ptx::smem_desc_kmajor(sa + 4 * TC_SLOT, 128, 512);
-                        const uint64_t bd = ptx::smem_desc_kmajor(sa + S * TC_SLOT, 128, 512);
+                        const uint8_t* sb = sa + G::A_SLOTS * TC_SLOT;
 #pragma unroll
-                        for (int ks = 0; ks < 2; ks++) {
-                            // the second K = 16 step starts two core matrices (256 bytes) further
-                            const uint32_t acc = (p > c0 || ks > 0) ? 1u : 0u;
-                            ptx::mma_f16_ss(tmem, a1 + (uint64_t)(ks * 16), bd + (uint64_t)(ks * 16), G::IDESC1, acc);
-                            if (G::N2 > 0)
-                                ptx::mma_f16_ss(tmem + (uint32_t)G::N1, a2 + (uint64_t)(ks * 16),
-                                                bd + (uint64_t)(ks * 16), G::IDESC2, acc);
+                        for (int sg = 0; sg < G::NSEG; sg++) {
+                            const int bslot = sg == 0 ? G::B_ZERO : (sg == 1 ? G::B_ZERO - 3 : G::B_ZERO - 4);
+                            const uint64_t ad = ptx::smem_desc_kmajor(sa + 4 * sg * TC_SLOT, 128, 512);
+                            const uint64_t bd = ptx::smem_desc_kmajor(sb + bslot * TC_SLOT, 128, 512);
+#pragma unroll
+                            for (int ks = 0; ks < 2; ks++) {
+                                // the second K = 16 step starts two core matrices (256 bytes) further
+                                const uint32_t acc = (p > c0 || sg > 0 || ks > 0) ? 1u : 0u;
+                                ptx::mma_f16_ss(d, ad + (uint64_t)(ks * 16), bd + (uint64_t)(ks * 16), G::IDESC, acc);
+                            }
                         }
                         ptx::mma_commit(&empty[st]);
                     }
-                    if (ok) ptx::mma_commit(tfull);
+                    if (ok) ptx::mma_commit(&tfull[tb]);
                 }
             }
             ptx::mma_commit(drain);
             if (!ptx::mbar_wait_bounded(drain, 0, TC_WAIT_NS)) on_timeout();
         }
+    } else if (warp < 2 + TC_DRAIN) {
+        // ------------------------------------------------------------- drain
+        // warp q (TMEM lane quadrant q = warp % 4, row i = lane): per chunk, the
+        // slots (q, u) for u = 1 .. s - q hold level q + 1 + u (every other slot
+        // is beyond level s + 1); each is read, converted once to int32 (exact:
+        // an integer below 2^24) and added into the C block's level sums in
+        // shared memory (the quadrants meet there: shared-memory atomics); then
+        // the TMEM buffer is released for the chunk after next.
+        const int q = warp & 3;
+        const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16);
+        int64_t ci = 0, cbi = 0;
+        bool ok = true;
+        for (int64_t seq = blockIdx.x; seq < a.nC && ok; seq += gridDim.x, cbi++) {
+            const longlong2 cur = sched_range(a, seq);
+            const int buf = (int)(cbi & 1);
+            if (!warp_wait(&lfree[buf], (uint32_t)(((cbi >> 1) & 1) ^ 1), abort_flag)) {
+                if (!*abort_flag) on_timeout();
+                ok = false;
+                break;
+            }
+            int* ls = LS + buf * G::LSBUF + lane * TC_LROW;   // level 0, row lane
+            for (int64_t c0 = cur.x; c0 < cur.y; c0 += G::CHUNK, ci++) {
+                const int tb = (int)(ci & 1);
+                if (!warp_wait(&tfull[tb], (uint32_t)((ci >> 1) & 1), abort_flag)) {
+                    if (!*abort_flag) on_timeout();
+                    ok = false;
+                    break;
+                }
+                ptx::tc_fence_after();
+                for (int u = 1; u <= S - q; u++) {
+                    uint32_t x[32];
+                    ptx::tmem_ld_32x32b_x32(tl + (uint32_t)(tb * TC_ACC_COLS + (u - 1) * 32), x);
+                    ptx::tmem_wait_ld();
+                    int* row = ls + (q + u - 1) * 32 * TC_LROW;   // level q + 1 + u, index from level 2
+#pragma unroll
+                    for (int c = 0; c < 32; c++) atomicAdd(row + c, __float2int_rn(__uint_as_float(x[c])));
+                }
+                ptx::tc_fence_before();
+                ptx::mbar_arrive(&tempty[tb]);
+            }
+            if (!ok) break;
+            ptx::mbar_arrive(&lfull[buf]);   // this C block's level sums are complete
+        }
     } else {
-        // ---------------------------------------------------------- epilogue
-        // warp (q, r): TMEM lane quadrant q = warp % 4, columns 16 r .. 16 r + 15
-        // of every 32-column accumulator block; in the sum and the final
-        // stage thread (warp (q, r), lane) owns row i = lane, columns 4 ep .. 4 ep + 3
-        const int q = warp & 3, r = (warp - 2) >> 2, ep = q * TC_R + r;
-        const BlasUpd bu(a.alpha, a.beta);
-        const uint32_t tl = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(r * TC_COLS);
-        const int t1 = q + 1, t2 = S - q;                 // A slices of quadrant q in G1 and G2
-        const bool has2 = (G::N2 > 0) && (t2 >= 5);
-        const int sw = lane & 7;   // 16-byte chunks XOR-swizzled by row: conflict-free stores and loads
+        // ------------------------------------------------------------ finish
+        // thread (finish warp fw, lane) owns row i = lane, columns TC_EL fw ..:
+        // it reads and zeroes the C block's level sums, hands the buffer back,
+        // recombines exactly, rounds once, applies alpha / beta and stores --
+        // while the drain warps accumulate the next C block.
+        const int fw = warp - 2 - TC_DRAIN;
         const int i = lane;
-        int64_t ci = 0;
+        const BlasUpd bu(a.alpha, a.beta);
+        int64_t cbi = 0;
         bool ok = true;
         TcBlk nxt;
         if (blockIdx.x < a.nC) nxt = a.sched[blockIdx.x];
-        for (int64_t seq = blockIdx.x; seq < a.nC && ok; seq += gridDim.x) {
+        for (int64_t seq = blockIdx.x; seq < a.nC && ok; seq += gridDim.x, cbi++) {
             const TcBlk cur = nxt;
             if (seq + gridDim.x < a.nC) nxt = a.sched[seq + gridDim.x];
-            // what the final stage needs, loaded now: its latency hides behind the MMAs
+            // what the recombination needs, loaded before the wait
             const bool row_ok = i < cur.m;
             const int ei = row_ok ? a.e[cur.rbase + i] : 0;
             int fj[TC_EL];
             double oldv[TC_EL];
 #pragma unroll
             for (int k = 0; k < TC_EL; k++) {
-                const int j = TC_EL * ep + k;
+                const int j = TC_EL * fw + k;
                 fj[k] = j < cur.n ? a.f[cur.cbase + j] : 0;
                 oldv[k] = (row_ok && j < cur.n && cur.old_off >= 0) ? a.Cold[cur.old_off + (int64_t)j * cur.m + i] : 0.0;
             }
+            const int buf = (int)(cbi & 1);
+            if (!warp_wait(&lfull[buf], (uint32_t)((cbi >> 1) & 1), abort_flag)) {
+                if (!*abort_flag) on_timeout();
+                ok = false;
+                break;
+            }
             int lv[S][TC_EL];
+            int* ls = LS + buf * G::LSBUF + i * TC_LROW + TC_EL * fw;
 #pragma unroll
             for (int d = 0; d < S; d++)
 #pragma unroll
-                for (int k = 0; k < TC_EL; k++) lv[d][k] = 0;
-            for (int64_t c0 = cur.p0; c0 < cur.p1; c0 += TC_CHUNK, ci++) {
-                const uint32_t ph = (uint32_t)(ci & 1);
-                if (!warp_wait(tfull, ph, abort_flag) || !warp_wait(sfree, ph ^ 1u, abort_flag)) {
-                    if (!*abort_flag) on_timeout();
-                    ok = false;
-                    break;
+                for (int k = 0; k < TC_EL; k++) {
+                    lv[d][k] = ls[d * 32 * TC_LROW + k];
+                    ls[d * 32 * TC_LROW + k] = 0;
                 }
-                ptx::tc_fence_after();
-                // 1. drain, two levels per TMEM round trip: level d of slice t1
-                //    (G1, u = d - t1) plus slice t2 (G2, u = d - t2) where it exists;
-                //    exact fp32 integers -> int32 level blocks
-                if (t1 <= S) {
-                    for (int d0 = t1 + 1; d0 <= S + 1; d0 += 2) {
-                        const int d1 = d0 + 1;
-                        const bool h1 = d1 <= S + 1;
-                        const bool g0 = has2 && d0 - t2 >= 1, g1 = has2 && h1 && d1 - t2 >= 1;
-                        uint32_t ra[TC_COLS], rb[TC_COLS], rc[TC_COLS], rd[TC_COLS];
-                        ptx::tmem_ld_32x32b_x16(tl + (uint32_t)((d0 - t1 - 1) * 32), ra);
-                        if (h1) ptx::tmem_ld_32x32b_x16(tl + (uint32_t)((d1 - t1 - 1) * 32), rb);
-                        if (g0) ptx::tmem_ld_32x32b_x16(tl + (uint32_t)(G::N1 + (d0 - t2 - 1) * 32), rc);
-                        if (g1) ptx::tmem_ld_32x32b_x16(tl + (uint32_t)(G::N1 + (d1 - t2 - 1) * 32), rd);
-                        ptx::tmem_wait_ld();
-                        uint8_t* row0 = stg + lvl_blk<S>(q, d0) * 4096 + lane * 128;
-                        uint8_t* row1 = stg + lvl_blk<S>(q, h1 ? d1 : d0) * 4096 + lane * 128;
-#pragma unroll
-                        for (int c = 0; c < TC_COLS / 4; c++) {
-                            int v0[4], v1[4];
-#pragma unroll
-                            for (int k = 0; k < 4; k++) {
-                                // both pair sums are integers below 2^23: their fp32 sum is exact
-                                float x0 = __uint_as_float(ra[c * 4 + k]);
-                                if (g0) x0 += __uint_as_float(rc[c * 4 + k]);
-                                float x1 = __uint_as_float(rb[c * 4 + k]);
-                                if (g1) x1 += __uint_as_float(rd[c * 4 + k]);
-                                v0[k] = __float2int_rn(x0);
-                                v1[k] = __float2int_rn(x1);
-                            }
-                            const int off = ((r * (TC_COLS / 4) + c) ^ sw) << 4;
-                            *reinterpret_cast<int4*>(row0 + off) = make_int4(v0[0], v0[1], v0[2], v0[3]);
-                            if (h1) *reinterpret_cast<int4*>(row1 + off) = make_int4(v1[0], v1[1], v1[2], v1[3]);
-                        }
-                    }
-                }
-                ptx::tc_fence_before();
-                ptx::mbar_arrive(tempty);
-                ptx::mbar_arrive(sfull);
-                if (!warp_wait(sfull, ph, abort_flag)) {
-                    if (!*abort_flag) on_timeout();
-                    ok = false;
-                    break;
-                }
-                // 2. level sums of this thread's four elements
-#pragma unroll
-                for (int d = 2; d <= S + 1; d++)
-#pragma unroll
-                    for (int w = 0; w < G::T1; w++)
-                        if (w + 2 <= d) {
-                            const int4 x = *reinterpret_cast<const int4*>(stg + lvl_blk<S>(w, d) * 4096 + lane * 128 +
-                                                                          ((ep ^ sw) << 4));
-                            lv[d - 2][0] += x.x;
-                            lv[d - 2][1] += x.y;
-                            lv[d - 2][2] += x.z;
-                            lv[d - 2][3] += x.w;
-                        }
-                ptx::mbar_arrive(sfree);
-            }
-            if (!ok) break;
-            // 3. exact recombination, one rounding, alpha / beta, column-major C block.
+            ptx::mbar_arrive(&lfree[buf]);
+            // exact recombination, one rounding, alpha / beta, column-major C block.
             // sum_d G_d 2^(7(s-1-d)) (d from 0) = U 2^(7 (s - NU)) + V with U over the
             // first NU = min(4, s) levels and V over the rest: |U|, |V| < 2^53, so
             // both run in int64 and one 128-bit shift and add joins them.
             constexpr int NU = S < 4 ? S : 4;
-            // the four elements are computed unconditionally (independent chains
-            // the scheduler can interleave); only the stores are guarded
             double res[TC_EL];
 #pragma unroll
             for (int k = 0; k < TC_EL; k++) {
@@ -453,7 +468,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_smm_emul_tc(TcArgs a) {
                 double* cout = a.Cd + cur.c_off;
 #pragma unroll
                 for (int k = 0; k < TC_EL; k++) {
-                    const int j = TC_EL * ep + k;
+                    const int j = TC_EL * fw + k;
                     if (j < cur.n) cout[(int64_t)j * cur.m + i] = res[k];
                 }
             }
@@ -477,7 +492,7 @@ int launch_tc(const TcArgs& a, int grid) {
 template <int S>
 double issued_per_product() {
     using G = TcGeo<S>;
-    return 2.0 * 128.0 * (double)(G::N1 + G::N2) * 32.0;
+    return 2.0 * 128.0 * (double)G::N * 32.0 * (double)G::NSEG;
 }
 
 }  // namespace
