@@ -41,10 +41,11 @@
 //     once to int32 and adds it into level q + 1 + u of the C block's level
 //     sums in shared memory (int32 atomics: the four quadrants contribute to
 //     the same levels); then releases the TMEM buffer.
-//   finish warps: once a C block's level sums are complete, each thread (row
-//     i = lane, four columns) reads and zeroes its level sums, hands the buffer
-//     back, recombines exactly, rounds, scales and stores -- while the drain
-//     warps fill the other of the two level-sum buffers with the next C block.
+//   finish warps: once a C block's level sums are complete, the 256 threads
+//     take its m x n elements in column-major order (one to four each): read
+//     and zero the element's level sums, hand the buffer back, recombine
+//     exactly, round, scale and store -- while the drain warps fill the other
+//     of the two level-sum buffers with the next C block.
 // int32 level sums are exact while products * s * 32 * 127^2 < 2^31 (checked
 // on the host). Every wait is bounded (4 s): on expiry the kernel sets the
 // error flag, the other roles see the abort flag, every role leaves its loop
@@ -63,7 +64,7 @@ namespace {
 constexpr int TC_DRAIN = 4;                   // drain warps: one per TMEM lane quadrant
 constexpr int TC_FIN = 8;                     // finish warps
 constexpr int TC_THREADS = 64 + 32 * (TC_DRAIN + TC_FIN);   // producer warp, MMA warp, drain, finish
-constexpr int TC_EL = 32 / TC_FIN;            // C elements (columns of a row) per finish thread
+constexpr int TC_EL = 32 / TC_FIN;            // most C elements per finish thread (32 x 32 over 256 threads)
 constexpr int TC_LROW = 33;                   // level-sum row stride in words: rows and columns conflict-free
 constexpr int TC_SLOT = 2048;                 // one 32 x 32 bf16 slice
 constexpr int TC_SMEM_CAP = 232448;           // 227 KB of shared memory per CTA
@@ -406,12 +407,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_smm_emul_tc(TcArgs a) {
         }
     } else {
         // ------------------------------------------------------------ finish
-        // thread (finish warp fw, lane) owns row i = lane, columns TC_EL fw ..:
-        // it reads and zeroes the C block's level sums, hands the buffer back,
-        // recombines exactly, rounds once, applies alpha / beta and stores --
-        // while the drain warps accumulate the next C block.
-        const int fw = warp - 2 - TC_DRAIN;
-        const int i = lane;
+        // finish thread ft takes the C block's elements e = ft, ft + 256, ..
+        // below m n (column-major: row e % m, column e / m, so consecutive
+        // threads store consecutive addresses and a small block keeps few
+        // threads busy for little time): it reads and zeroes the element's level
+        // sums, hands the buffer back, recombines exactly, rounds once, applies
+        // alpha / beta and stores -- while the drain warps accumulate the next
+        // C block. Level sums outside m x n are never written (zero padding).
+        const int ft = (warp - 2 - TC_DRAIN) * 32 + lane;
+        constexpr int NFT = 32 * TC_FIN;
         const BlasUpd bu(a.alpha, a.beta);
         int64_t cbi = 0;
         bool ok = true;
@@ -420,16 +424,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_smm_emul_tc(TcArgs a) {
         for (int64_t seq = blockIdx.x; seq < a.nC && ok; seq += gridDim.x, cbi++) {
             const TcBlk cur = nxt;
             if (seq + gridDim.x < a.nC) nxt = a.sched[seq + gridDim.x];
+            const int mn = cur.m * cur.n;
             // what the recombination needs, loaded before the wait
-            const bool row_ok = i < cur.m;
-            const int ei = row_ok ? a.e[cur.rbase + i] : 0;
-            int fj[TC_EL];
+            int ri[TC_EL], cj[TC_EL], ex[TC_EL];
             double oldv[TC_EL];
 #pragma unroll
             for (int k = 0; k < TC_EL; k++) {
-                const int j = TC_EL * fw + k;
-                fj[k] = j < cur.n ? a.f[cur.cbase + j] : 0;
-                oldv[k] = (row_ok && j < cur.n && cur.old_off >= 0) ? a.Cold[cur.old_off + (int64_t)j * cur.m + i] : 0.0;
+                const int e = ft + NFT * k;
+                const bool in = e < mn;
+                ri[k] = in ? e % cur.m : 0;
+                cj[k] = in ? e / cur.m : 0;
+                ex[k] = in ? a.e[cur.rbase + ri[k]] + a.f[cur.cbase + cj[k]] : 0;
+                oldv[k] = (in && cur.old_off >= 0) ? a.Cold[cur.old_off + e] : 0.0;
             }
             const int buf = (int)(cbi & 1);
             if (!warp_wait(&lfull[buf], (uint32_t)((cbi >> 1) & 1), abort_flag)) {
@@ -438,39 +444,36 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_smm_emul_tc(TcArgs a) {
                 break;
             }
             int lv[S][TC_EL];
-            int* ls = LS + buf * G::LSBUF + i * TC_LROW + TC_EL * fw;
+            int* lsb = LS + buf * G::LSBUF;
 #pragma unroll
-            for (int d = 0; d < S; d++)
+            for (int k = 0; k < TC_EL; k++) {
+                int* ls = lsb + ri[k] * TC_LROW + cj[k];
+                const bool in = ft + NFT * k < mn;
 #pragma unroll
-                for (int k = 0; k < TC_EL; k++) {
-                    lv[d][k] = ls[d * 32 * TC_LROW + k];
-                    ls[d * 32 * TC_LROW + k] = 0;
+                for (int d = 0; d < S; d++) {
+                    lv[d][k] = in ? ls[d * 32 * TC_LROW] : 0;
+                    if (in) ls[d * 32 * TC_LROW] = 0;
                 }
+            }
             ptx::mbar_arrive(&lfree[buf]);
             // exact recombination, one rounding, alpha / beta, column-major C block.
             // sum_d G_d 2^(7(s-1-d)) (d from 0) = U 2^(7 (s - NU)) + V with U over the
             // first NU = min(4, s) levels and V over the rest: |U|, |V| < 2^53, so
             // both run in int64 and one 128-bit shift and add joins them.
             constexpr int NU = S < 4 ? S : 4;
-            double res[TC_EL];
+            double* cout = a.Cd + cur.c_off;
 #pragma unroll
             for (int k = 0; k < TC_EL; k++) {
+                const int e = ft + NFT * k;
+                if (e >= mn) break;
                 long long U = 0, V = 0;
 #pragma unroll
                 for (int d = 0; d < NU; d++) U = U * 128 + lv[d][k];
 #pragma unroll
                 for (int d = NU; d < S; d++) V = V * 128 + lv[d][k];
                 const __int128 Sx = (__int128)U * ((__int128)1 << (7 * (S - NU))) + V;
-                const double x = emul::round_i128_scaled(Sx, ei + fj[k] - 7 * (S + 1));
-                res[k] = cur.old_off >= 0 ? bu.update(x, oldv[k]) : bu.scale(x);
-            }
-            if (row_ok) {
-                double* cout = a.Cd + cur.c_off;
-#pragma unroll
-                for (int k = 0; k < TC_EL; k++) {
-                    const int j = TC_EL * fw + k;
-                    if (j < cur.n) cout[(int64_t)j * cur.m + i] = res[k];
-                }
+                const double x = emul::round_i128_scaled(Sx, ex[k] - 7 * (S + 1));
+                cout[e] = cur.old_off >= 0 ? bu.update(x, oldv[k]) : bu.scale(x);
             }
         }
     }
