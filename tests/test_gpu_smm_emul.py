@@ -61,11 +61,25 @@ def test_uneven_blocks_transposes_beta(ta, tb, kernel):
 @pytest.mark.parametrize("nk", [32, 33, 70])
 def test_long_product_lists_chunked(nk, kernel):
     # one C block row x one C block column, nk products per C block: the
-    # tcgen05 kernel's fp32 accumulators are flushed every 32 products
+    # tcgen05 kernel's fp32 accumulators are flushed every 16 products
     rng = np.random.default_rng(630 + nk)
     A, B, Cm = synth.random_small(rng, 2, nk, 3, p=1.0, sizes=(32,), dist="wide", with_c=True, c_p=1.0)
     got, _ = gpu_multiply("N", "N", -1.5, A, B, 0.25, Cm, path="stacks", precision="ozaki", kernel=kernel)
     ref, _, _ = emul_ref("N", "N", A, B, Cm, -1.5, 0.25, 7)
+    assert_same_pattern(got, ref)
+    assert np.array_equal(got.data, ref.data)
+
+
+@pytest.mark.parametrize("s", [8, 5, 4])
+def test_long_product_lists_every_segment_count(s):
+    # 23 products per C block: several exact fp32 stretches (16 products with
+    # one or two operand segments, 10 with three at s = 8) alternating between
+    # the two TMEM accumulators, on the tcgen05 kernel; wide-range values
+    rng = np.random.default_rng(640 + s)
+    A, B, Cm = synth.random_small(rng, 2, 23, 3, p=1.0, sizes=(32, 29), dist="wide", with_c=True, c_p=1.0)
+    got, _ = gpu_multiply("N", "T", 0.75, A, synth.transpose_blocks(B), -2.0, Cm, path="stacks",
+                          precision="ozaki", ozaki_slices=s, kernel=2)
+    ref, _, _ = emul_ref("N", "N", A, B, Cm, 0.75, -2.0, s)
     assert_same_pattern(got, ref)
     assert np.array_equal(got.data, ref.data)
 
