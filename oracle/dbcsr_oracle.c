@@ -343,7 +343,8 @@ int oracle_multiply(char ta, char tb, double alpha, const ob_mat *A, const ob_ma
  * one kind); the canonical order used for comparison is: shape (m,n,k)
  * ascending, then i, then j, then k. A stack is a maximal run of entries of
  * one shape, cut every stack_cap entries. Each entry is written as 7 ints:
- * stack id, m, n, k, i, j, kblk. Returns the number of entries, or <0.
+ * stack id, m, n, k, i, j, kblk. Returns the number of entries, or <0
+ * (-1 duplicate block, -2 block grids or inner block sizes that disagree).
  * ------------------------------------------------------------------------- */
 static int cmp_entry(const void *x, const void *y)
 {
@@ -360,6 +361,8 @@ int64_t oracle_stack_list(char ta, char tb, const ob_mat *A, const ob_mat *B,
     if (rows_build(A, ta, &a)) return -1;
     if (rows_build(B, tb, &b)) { rows_free(&a); return -1; }
     if (a.nbc != b.nbr) { rows_free(&a); rows_free(&b); return -2; }
+    for (int k = 0; k < a.nbc; k++)   /* every product needs A's k size == B's */
+        if (a.cs[k] != b.rs[k]) { rows_free(&a); rows_free(&b); return -2; }
     int64_t n = 0;
     for (int i = 0; i < a.nbr; i++)
         for (int64_t p = a.rowptr[i]; p < a.rowptr[i + 1]; p++) {

@@ -127,6 +127,18 @@ def test_alpha_beta_and_row_subset():
     assert np.array_equal(np.delete(sub, [1, 4], 0), np.delete(C0, [1, 4], 0))
 
 
+def test_beta_zero_never_reads_old_c():
+    # beta = 0: C is output only, as in the plain product -- a NaN there does not propagate
+    rng = np.random.default_rng(56)
+    A = np.asfortranarray(rng.uniform(-1, 1, (6, 9)))
+    B = np.asfortranarray(rng.uniform(-1, 1, (9, 5)))
+    nan = np.full((6, 5), np.nan, order="F")
+    O.ozaki_gemm(1.0, A, B, 0.0, nan, s=7)
+    zero = np.zeros((6, 5), order="F")
+    O.ozaki_gemm(1.0, A, B, 0.0, zero, s=7)
+    assert np.array_equal(nan, zero)
+
+
 def test_round_tf32_known_values():
     # TF32 keeps 10 mantissa bits: ulp(1) = 2^-10; 2^-11 is a tie, rounded away from zero
     assert O.round_tf32([1.0 + 2.0 ** -11])[0] == 1.0 + 2.0 ** -10

@@ -185,6 +185,39 @@ def test_dimension_mismatch_rejected():
         O.multiply("N", "N", 1.0, A, Bbad, 0.0)
 
 
+def test_inner_block_size_mismatch_rejected():
+    # same number of block columns in A as block rows in B, but one k block of
+    # A is narrower than B's: no block product is defined (Sec. II)
+    one = np.array([2], np.int32)
+    z = np.zeros(1, np.int32)
+    A = synth.BlockSparse(one, np.array([2, 3], np.int32), np.zeros(2, np.int32), np.array([0, 1], np.int32),
+                          np.ones(2 * 2 + 2 * 3))
+    B = synth.BlockSparse(np.array([3, 3], np.int32), one, np.array([0, 1], np.int32), np.zeros(2, np.int32),
+                          np.ones(3 * 2 + 3 * 2))
+    with pytest.raises(ValueError):
+        O.multiply("N", "N", 1.0, A, B, 0.0)
+    with pytest.raises(ValueError):
+        O.stack_list("N", "N", A, B)
+    # the same check through op(): A^T with A stored 3 x 2 has a k size of 2
+    At = synth.BlockSparse(np.array([2, 3], np.int32), one, np.array([0, 1], np.int32), z.repeat(2),
+                           np.ones(2 * 2 + 3 * 2))
+    with pytest.raises(ValueError):
+        O.multiply("T", "N", 1.0, At, B, 0.0)
+
+
+def test_duplicate_block_rejected():
+    # a block index names each (row, column) at most once (blocked CSR, Sec. II)
+    rs = np.array([2, 2], np.int32)
+    A = synth.BlockSparse(rs, rs, np.array([0, 1, 0], np.int32), np.array([1, 0, 1], np.int32), np.ones(12))
+    B = synth.BlockSparse(rs, rs, np.array([0, 1], np.int32), np.array([0, 1], np.int32), np.ones(8))
+    with pytest.raises(ValueError):
+        O.multiply("N", "N", 1.0, A, B, 0.0)
+    with pytest.raises(ValueError):
+        O.multiply("N", "N", 1.0, B, A, 0.0)
+    with pytest.raises(ValueError):
+        O.stack_list("N", "N", A, B)
+
+
 def test_row_subset_equals_full_rows():
     rng = np.random.default_rng(20)
     A, B, Cm = synth.random_small(rng, 7, 5, 6, p=0.5, with_c=True)
