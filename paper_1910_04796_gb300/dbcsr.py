@@ -116,6 +116,33 @@ def init(stream=None):
     _check(load().dbcsr_init(C.c_void_p(handle)))
 
 
+def set_allocator(alloc=None, free=None):
+    """Route device allocations through Python callables (dbcsr_set_allocator).
+
+    ``alloc(nbytes, stream)`` returns a device address (int), or None to refuse;
+    ``free(ptr, nbytes, stream)`` takes back what ``alloc`` gave. Both None
+    restores the library's own stream-ordered pool. The library returns every
+    block to the hook that made it, even after a switch, so the callables are
+    kept alive for the life of the process.
+    """
+    L = load()
+    if alloc is None and free is None:
+        _check(L.dbcsr_set_allocator(ALLOC_FN(), FREE_FN(), None))
+        return
+    if alloc is None or free is None:
+        raise ValueError("set_allocator: give both alloc and free, or neither")
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return alloc(int(nbytes), stream or 0)
+        except Exception:  # an exception must not cross into C: report a refusal
+            return None
+
+    fa = ALLOC_FN(_alloc)
+    ff = FREE_FN(lambda ptr, nbytes, stream, ctx: free(ptr, int(nbytes), stream or 0))
+    _keep.extend([fa, ff])
+    _check(L.dbcsr_set_allocator(fa, ff, None))
+
+
 def use_torch_allocator(enable: bool = True):
     """Route the library's device allocations through PyTorch's caching allocator."""
     import torch
