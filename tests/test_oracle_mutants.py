@@ -49,6 +49,9 @@ MUTANTS = [
     ("old accumulator not carried between k blocks", C_SRC,
      "double sum = x[r + (int64_t)cc * m];",
      "double sum = 0.0;"),
+    ("product and sum fused into one rounding (FMA)", C_SRC,
+     "sum = sum + ablk[r + (int64_t)l * m] * bblk[l + (int64_t)cc * kk];",
+     "sum = fma(ablk[r + (int64_t)l * m], bblk[l + (int64_t)cc * kk], sum);"),
     ("alpha and beta swapped", C_SRC,
      "double r = alpha * v;\n                    if (old) r = r + beta * old[e];",
      "double r = beta * v;\n                    if (old) r = r + alpha * old[e];"),
@@ -74,6 +77,9 @@ MUTANTS = [
     ("Dot2: TwoSum error dropped", C_SRC,
      "sl = sl + (pe + te);",
      "sl = sl + pe;"),
+    ("Dot2: TwoProduct error dropped", C_SRC,
+     "sl = sl + (pe + te);",
+     "sl = sl + te;"),
     ("Dot2: compensation not added at the end", C_SRC,
      "double v = (mode == 1) ? acc[j][e] + cmp[j][e] : acc[j][e];",
      "double v = acc[j][e];"),
@@ -92,6 +98,9 @@ MUTANTS = [
     ("stack cut one entry late", C_SRC,
      "if (newshape || run == stack_cap)",
      "if (newshape || run == stack_cap + 1)"),
+    ("stack counter not reset at a new shape", C_SRC,
+     "if (newshape || run == stack_cap) { sid++; run = 0; }",
+     "if (newshape || run == stack_cap) { sid++; if (!newshape) run = 0; }"),
     ("stack shape written as (m, k, n)", C_SRC,
      "x[1] = a.rs[i]; x[2] = b.cs[j]; x[3] = a.cs[k];",
      "x[1] = a.rs[i]; x[2] = a.cs[k]; x[3] = b.cs[j];"),
@@ -118,6 +127,12 @@ MUTANTS = [
     ("exponent one too small", C_SRC,
      "(void)frexp(mu, &e);\n    return e;",
      "(void)frexp(mu, &e);\n    return e - 1;"),
+    ("row maximum taken as its last element", C_SRC,
+     "for (int64_t l = 0; l < K; l++) { double v = fabs(A[i + l * lda]); if (v > mu) mu = v; }",
+     "for (int64_t l = 0; l < K; l++) { double v = fabs(A[i + l * lda]); mu = v; }"),
+    ("dense GEMM: product and sum fused (FMA)", C_SRC,
+     "s = s + x * y;",
+     "s = fma(x, y, s);"),
     ("column maximum taken as its last element", C_SRC,
      "for (int64_t l = 0; l < K; l++) { double v = fabs(B[l + j * ldb]); if (v > nu) nu = v; }",
      "for (int64_t l = 0; l < K; l++) { double v = fabs(B[l + j * ldb]); nu = v; }"),
