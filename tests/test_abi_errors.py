@@ -111,3 +111,11 @@ def test_noalloc_gemm_argument_checks(L):
         assert msg in last(L)
     # empty products are complete without any device work
     assert f(0, 5, 3, 1.0, None, 1, None, 3, 0.0, None, 1, 0, None) == dbcsr.OK
+
+
+def test_binding_allocator_hooks_come_in_pairs(L):
+    with pytest.raises(ValueError):
+        dbcsr.set_allocator(lambda nbytes, stream: None, None)
+    with pytest.raises(ValueError):
+        dbcsr.set_allocator(None, lambda ptr, nbytes, stream: None)
+    dbcsr.set_allocator(None, None)   # the built-in pool: accepted without a GPU
