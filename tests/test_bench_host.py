@@ -1,0 +1,97 @@
+"""Host logic of bench.py that needs no GPU (CPU only).
+
+* roofline.traffic: the DRAM bytes recorded from an ncu capture are reported
+  only while the kernel's source file still has the SHA-256 recorded with them,
+  so a number taken on older code is never reported for newer code;
+* the clock summary taken from nvidia-smi samples (median SM clock, maximum,
+  throttle reasons seen);
+* the roofline denominators: MEASURED_PEAKS.json, else the stated fallback.
+"""
+import hashlib
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def _table(tmp_path, src_rel, sha, value, workload="w-small", precision="ozaki", path="dense"):
+    t = tmp_path / "traffic.md"
+    t.write_text(
+        "| workload | precision | path | kernel | source | sha256 | dram bytes per launch |\n"
+        "|---|---|---|---|---|---|---|\n"
+        f"| {workload} | {precision} | {path} | k_x | {src_rel} | {sha} | {value} |\n")
+    return str(t)
+
+
+def test_traffic_reported_only_for_the_recorded_source(tmp_path, monkeypatch):
+    src = tmp_path / "kernel.cu"
+    src.write_bytes(b"__global__ void k_x() {}\n")
+    sha = hashlib.sha256(src.read_bytes()).hexdigest()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "TRAFFIC_TABLE", _table(tmp_path, "kernel.cu", sha, 123456789))
+    assert bench.dram_traffic("w-small", "ozaki", "dense") == 123456789.0
+    # another workload, precision or path has no number
+    assert bench.dram_traffic("w-other", "ozaki", "dense") is None
+    assert bench.dram_traffic("w-small", "fp64", "dense") is None
+    assert bench.dram_traffic("w-small", "ozaki", "stacks") is None
+    # the kernel changed after the capture: the number is withheld
+    src.write_bytes(b"__global__ void k_x() { /* changed */ }\n")
+    assert bench.dram_traffic("w-small", "ozaki", "dense") is None
+
+
+def test_traffic_missing_or_malformed_gives_none(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "TRAFFIC_TABLE", str(tmp_path / "absent.md"))
+    assert bench.dram_traffic("w-small", "ozaki", "dense") is None
+    src = tmp_path / "kernel.cu"
+    src.write_bytes(b"x")
+    sha = hashlib.sha256(b"x").hexdigest()
+    monkeypatch.setattr(bench, "TRAFFIC_TABLE", _table(tmp_path, "kernel.cu", sha, "n/a"))
+    assert bench.dram_traffic("w-small", "ozaki", "dense") is None
+    monkeypatch.setattr(bench, "TRAFFIC_TABLE", _table(tmp_path, "gone.cu", sha, 5))
+    assert bench.dram_traffic("w-small", "ozaki", "dense") is None
+
+
+def test_committed_traffic_rows_name_existing_sources():
+    rows = [ln for ln in open(bench.TRAFFIC_TABLE).read().splitlines() if ln.count("|") == 8]
+    data = [[c.strip() for c in r.strip().strip("|").split("|")] for r in rows[2:]]
+    assert data, "no traffic rows"
+    for cells in data:
+        assert os.path.exists(os.path.join(ROOT, cells[4])), cells[4]
+        assert len(cells[5]) == 64 and int(cells[5], 16) >= 0
+        assert float(cells[6]) > 0
+
+
+def test_clock_summary():
+    c = bench.Clocks()
+    c.lines = [
+        "1965, 2070, 1180.2, Not Active, Not Active, Not Active, Active",
+        "1890, 2070, 1201.0, Not Active, Not Active, Not Active, Active",
+        "2010, 2070, 1150.7, Not Active, Not Active, Not Active, Not Active",
+        "garbage line",
+        "[N/A], 2070, 1, Not Active, Not Active, Not Active, Not Active",
+    ]
+    s = c.summary()
+    assert s == {"sm_mhz": 1965.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    c.lines.append("1200, 2070, 900.0, Active, Not Active, Active, Not Active")
+    assert c.summary()["reasons"] == ["hw_slowdown", "sw_power_cap", "sw_thermal_slowdown"]
+    empty = bench.Clocks()
+    assert empty.summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+
+
+def test_peaks_measured_else_fallback(tmp_path, monkeypatch):
+    p, src = bench.peaks()
+    if os.path.exists(bench.PEAKS_FILE):
+        assert src == "measured" and p["hbm_gbs"] > 0 and p["bf16_tflops"] > 0
+    monkeypatch.setattr(bench, "PEAKS_FILE", str(tmp_path / "absent.json"))
+    p, src = bench.peaks()
+    assert src == "fallback"
+    assert (p["hbm_gbs"], p["bf16_tflops"], p["bf16_tflops_sustained"]) == (6800.0, 1900.0, 1700.0)
+
+
+def test_aggregate_value_counts_every_replica():
+    # two replicas, 5 steps of 2e12 useful flops each, in 4 s: 5 TFLOP/s for the job
+    assert bench.aggregate_value(2.0e12, 2, 5, 4.0) == 5.0
