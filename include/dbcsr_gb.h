@@ -70,7 +70,12 @@ typedef void (*dbcsr_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
 
 /* Execution path of dbcsr_multiply (Sec. II stacks vs Sec. III densification). */
 #define DBCSR_PATH_AUTO   0  /* dense path when op(A) and op(B) are 100% occupied, else stacks */
-#define DBCSR_PATH_STACKS 1  /* stacks of block products, batched small-GEMM kernels */
+#define DBCSR_PATH_STACKS 1  /* stacks of block products, batched small-GEMM kernels. FP64
+                                and FP32: any block size. Emulated FP64: block edges up
+                                to 32 (DBCSR_ERR_ARG above). TF32: none (DBCSR_ERR_ARG). So
+                                sparse operands with larger blocks (emulated) or in TF32
+                                need DBCSR_PATH_DENSE or DBCSR_PATH_HYBRID, chosen
+                                explicitly: AUTO does not switch on block size */
 #define DBCSR_PATH_DENSE  2  /* densify, one GEMM, undensify (any occupancy; absent blocks = 0) */
 #define DBCSR_PATH_HYBRID 3  /* per panel of block rows of op(A): densified GEMM where the panel
                                 (and op(B)) is at least hybrid_fill_pct % occupied, stacks elsewhere
