@@ -4,8 +4,9 @@
  * A plain, slow, obviously correct CPU statement of what the GPU library
  * computes, written from the paper (Sivkov, Lazzaro, Hutter: "DBCSR: A Library
  * for Dense Matrix Multiplications on Distributed GPU-Accelerated Systems").
- * Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may load
- * it. It shares no code, header or table with the CUDA library.
+ * Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg and
+ * reference arm (the oracle timed on the host cores) may load it. It shares no
+ * code, header or table with the CUDA library.
  *
  * What it states:
  *   - the local block-sparse product C = alpha*op(A)*op(B) + beta*C on the
