@@ -230,7 +230,7 @@ def run_reference(args, world, rank):
     threads = O.threads()
     rows = list(range(0, nrows, max(1, nrows // max(1, args.ref_rows))))[:args.ref_rows]
     vals = []
-    for _ in range(args.warmup if args.warmup < 2 else 1):
+    for _ in range(args.warmup):   # warm-up steps of one C block row each
         cpu_oracle_sample(w, rows[:1], threads)
     flops_tot, t_tot = 0.0, 0.0
     for _ in range(args.steps):
@@ -245,7 +245,7 @@ def run_reference(args, world, rank):
         "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000.0 * t_tot / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name, "sample": sample},
+        "config": {"workload": w.name, "sample": sample, "warmup_sample": "one C block row per warm-up step"},
         "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }

@@ -95,3 +95,16 @@ def test_peaks_measured_else_fallback(tmp_path, monkeypatch):
 def test_aggregate_value_counts_every_replica():
     # two replicas, 5 steps of 2e12 useful flops each, in 4 s: 5 TFLOP/s for the job
     assert bench.aggregate_value(2.0e12, 2, 5, 4.0) == 5.0
+
+
+def test_reference_arm_runs_on_rank_zero_only(capsys):
+    import argparse
+    args = argparse.Namespace(workload="small-sparse", scale=1.0, occ=0.1, steps=1, warmup=3, ref_rows=4)
+    assert bench.run_reference(args, 2, 1) == 0          # rank 1: no work, no line
+    assert capsys.readouterr().out == ""
+    assert bench.run_reference(args, 2, 0) == 0          # rank 0 prints the one line
+    import json
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["warmup"] == 3
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["value"] > 0
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
