@@ -5,7 +5,9 @@
   so a number taken on older code is never reported for newer code;
 * the clock summary taken from nvidia-smi samples (median SM clock, maximum,
   throttle reasons seen);
-* the roofline denominators: MEASURED_PEAKS.json, else the stated fallback.
+* the roofline denominators: MEASURED_PEAKS.json, else the stated fallback;
+* the reference arm (the oracle on the host cores) works and prints on rank 0
+  only, with the warm-up steps it reports.
 """
 import hashlib
 import os
