@@ -1,6 +1,7 @@
 """The oracle against hand-worked fixtures (tests/golden/): a stack list
-enumerated by hand, a 2 x 2 block product worked by hand, and integer slices of
-values with known binary expansions. The paper prints no numeric example, so
+enumerated by hand, a 2 x 2 block product worked by hand, integer slices of
+values with known binary expansions, and single-precision products rounded by
+hand. The paper prints no numeric example, so
 every value here is derived by hand from the definitions it states (Sec. II)."""
 import os
 
@@ -54,3 +55,16 @@ def test_block_product_matches_hand_result(r):
 def test_slices_match_hand_expansion(r):
     x, s = float(r[0]), int(r[1])
     assert O.ozaki_split(x, s) == [int(v) for v in r[2:]]
+
+
+@pytest.mark.parametrize("r", rows("fp32_rounding.txt"), ids=lambda r: r[0])
+def test_single_precision_matches_hand_rounding(r):
+    k = int(r[1])
+    a = np.array([float.fromhex(x) for x in r[2:2 + k]])
+    b = np.array([float.fromhex(x) for x in r[2 + k:2 + 2 * k]])
+    c32, c64 = float.fromhex(r[2 + 2 * k]), float.fromhex(r[3 + 2 * k])
+    one, kk, z = np.array([1], np.int32), np.array([k], np.int32), np.zeros(1, np.int32)
+    A = synth.BlockSparse(one, kk, z, z, a)
+    B = synth.BlockSparse(kk, one, z, z, b)
+    assert O.multiply("N", "N", 1.0, A, B, 0.0, mode=2).data[0] == c32
+    assert O.multiply("N", "N", 1.0, A, B, 0.0, mode=0).data[0] == c64

@@ -4,8 +4,8 @@ Each case copies ``oracle/`` into a temporary directory, plants one plausible
 mistake in the copy (a transposed operand, a dropped term, a wrong sign or
 index, alpha and beta swapped, a wrong stack cut, a dropped slice level, ...),
 builds it, and runs every pin test of ``test_oracle_pins.py``,
-``test_oracle_ozaki_pins.py`` and ``test_oracle_fp32_pins.py`` against the copy
-in a child process. The mistake must make at least one pin fail. The unchanged
+``test_oracle_ozaki_pins.py``, ``test_oracle_fp32_pins.py`` and the hand-worked
+fixtures of ``test_golden.py`` against the copy in a child process. The mistake must make at least one pin fail. The unchanged
 copy must pass them all, which shows that the child really runs the copy.
 
 Every planted mistake keeps all memory accesses inside their buffers (a changed
@@ -26,7 +26,7 @@ import pytest
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-PIN_MODULES = ("test_oracle_pins.py", "test_oracle_ozaki_pins.py", "test_oracle_fp32_pins.py")
+PIN_MODULES = ("test_oracle_pins.py", "test_oracle_ozaki_pins.py", "test_oracle_fp32_pins.py", "test_golden.py")
 
 C_SRC = "dbcsr_oracle.c"
 PY_SRC = "oracle.py"
