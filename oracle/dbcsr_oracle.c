@@ -456,11 +456,20 @@ int oracle_num_threads(void)
  *     dropped), G_d(i,j) = sum over t+u=d of sum_l sigmaA_t(i,l) sigmaB_u(l,j).
  *  4. Recombination, exact then rounded once: the integer
  *     S = sum_{d=2}^{s+1} G_d * 2^(7(s+1-d)) is formed exactly (128-bit), and
- *     acc = S * 2^(-7(s+1)) is S converted to FP64 with one rounding to
- *     nearest (ties to even), scaled by an exact power of two.
- *  5. C(i,j) = alpha * (acc * 2^(e_i + f_j)) + beta * C(i,j), where the
- *     product by 2^(e_i + f_j - 7(s+1)) is one ldexp of the rounded S.
+ *     the real number S * 2^(e_i + f_j - 7(s+1)) is rounded once to the
+ *     nearest double (ties to even) -- 53 significant bits for a normal
+ *     result, fewer for a subnormal one, +-infinity beyond the largest double.
+ *  5. C(i,j) = alpha * that value + beta * C(i,j).
+ *
+ * Non-finite inputs (a reading: the scheme is defined for finite values). A
+ * row of A, or a column of B, that holds a NaN or an infinity has no finite
+ * maximum to scale by. Its exponent is the marker OZ_NONFINITE, its slices are
+ * not formed, and every C(i,j) of that row i or column j is NaN -- whatever
+ * alpha, beta and the old C(i,j). (IEEE FP64 gives a NaN or an infinity in
+ * exactly those elements of a dense product: one non-finite term in a dot
+ * product makes it non-finite.)
  * ------------------------------------------------------------------------- */
+#define OZ_NONFINITE (1 << 20)
 static int frexp_exp(double mu)
 {
     int e = 0;
@@ -480,20 +489,69 @@ void oracle_ozaki_split(double x, int s, int *out)
     }
 }
 
-/* row exponents of column-major A (M x K), column exponents of column-major B (K x N) */
+/* row exponents of column-major A (M x K), column exponents of column-major B
+ * (K x N); OZ_NONFINITE for a row / column holding a NaN or an infinity */
 void oracle_ozaki_exponents(int64_t M, int64_t N, int64_t K, const double *A, int64_t lda,
                             const double *B, int64_t ldb, int *e_row, int *f_col)
 {
     for (int64_t i = 0; i < M; i++) {
         double mu = 0.0;
-        for (int64_t l = 0; l < K; l++) { double v = fabs(A[i + l * lda]); if (v > mu) mu = v; }
-        e_row[i] = frexp_exp(mu);
+        int finite = 1;
+        for (int64_t l = 0; l < K; l++) {
+            double v = fabs(A[i + l * lda]);
+            if (!isfinite(v)) finite = 0;
+            else if (v > mu) mu = v;
+        }
+        e_row[i] = finite ? frexp_exp(mu) : OZ_NONFINITE;
     }
     for (int64_t j = 0; j < N; j++) {
         double nu = 0.0;
-        for (int64_t l = 0; l < K; l++) { double v = fabs(B[l + j * ldb]); if (v > nu) nu = v; }
-        f_col[j] = frexp_exp(nu);
+        int finite = 1;
+        for (int64_t l = 0; l < K; l++) {
+            double v = fabs(B[l + j * ldb]);
+            if (!isfinite(v)) finite = 0;
+            else if (v > nu) nu = v;
+        }
+        f_col[j] = finite ? frexp_exp(nu) : OZ_NONFINITE;
     }
+}
+
+/* The real number S * 2^k rounded once to the nearest double, ties to even:
+ * keep the bits of |S| down to the last one a double can hold -- the 53rd
+ * significant bit, or the bit of weight 2^-1074 when the result is subnormal
+ * -- and round at that bit. The kept integer q (at most 2^53) times 2^(k+drop)
+ * is then exactly a double, or beyond the largest one (infinity, which is the
+ * correctly rounded result there). A nonzero S that rounds to zero gives a
+ * zero with its sign. */
+double oracle_round_scaled(__int128 S, int k)
+{
+    if (S == 0) return 0.0;
+    int neg = S < 0;
+    unsigned __int128 a = neg ? (unsigned __int128)0 - (unsigned __int128)S : (unsigned __int128)S;
+    int n = 0;                                   /* bit length of |S| */
+    for (unsigned __int128 t = a; t != 0; t >>= 1) n++;
+    int drop = n - 53;                           /* bits below a 53-bit significand */
+    if (n - 1 + k < -1022) drop = -1074 - k;     /* subnormal result */
+    double r;
+    if (drop <= 0) {
+        r = ldexp((double)a, k);                 /* a < 2^53: exact */
+    } else if (drop >= 128) {
+        r = 0.0;                                 /* |S| < 2^127 <= half of the last kept bit */
+    } else {
+        unsigned __int128 q = a >> drop;
+        unsigned __int128 rem = a - (q << drop);
+        unsigned __int128 half = (unsigned __int128)1 << (drop - 1);
+        if (rem > half || (rem == half && (q & 1))) q += 1;
+        r = ldexp((double)q, k + drop);          /* q <= 2^53: exact, or infinity */
+    }
+    return neg ? -r : r;
+}
+
+/* the same with S given as its two 64-bit halves (for the tests) */
+double oracle_round_scaled_parts(int64_t hi, uint64_t lo, int k)
+{
+    __int128 S = (__int128)(((unsigned __int128)(uint64_t)hi << 64) | lo);
+    return oracle_round_scaled(S, k);
 }
 
 /* The emulated product on column-major operands; only the rows in rows_sel
@@ -519,7 +577,8 @@ int oracle_ozaki_gemm(int64_t M, int64_t N, int64_t K, double alpha, const doubl
     for (int64_t j = 0; j < N; j++) {
         int sl[8];
         for (int64_t l = 0; l < K; l++) {
-            oracle_ozaki_split(ldexp(B[l + j * ldb], -f_col[j]), s, sl);
+            if (f_col[j] == OZ_NONFINITE) memset(sl, 0, sizeof(sl));   /* never used: C column is NaN */
+            else oracle_ozaki_split(ldexp(B[l + j * ldb], -f_col[j]), s, sl);
             for (int u = 0; u < s; u++) SB[((size_t)u * K + l) * N + j] = (signed char)sl[u];
         }
     }
@@ -533,7 +592,8 @@ int oracle_ozaki_gemm(int64_t M, int64_t N, int64_t K, double alpha, const doubl
             int64_t i = rows_sel ? rows_sel[q] : q;
             int sl[8];
             for (int64_t l = 0; l < K; l++) {
-                oracle_ozaki_split(ldexp(A[i + l * lda], -e_row[i]), s, sl);
+                if (e_row[i] == OZ_NONFINITE) memset(sl, 0, sizeof(sl));   /* never used: C row is NaN */
+                else oracle_ozaki_split(ldexp(A[i + l * lda], -e_row[i]), s, sl);
                 for (int t = 0; t < s; t++) SA[(size_t)t * K + l] = (signed char)sl[t];
             }
             memset(G, 0, sizeof(int64_t) * (size_t)(s + 2) * (size_t)N);
@@ -548,9 +608,13 @@ int oracle_ozaki_gemm(int64_t M, int64_t N, int64_t K, double alpha, const doubl
                     }
                 }
             for (int64_t j = 0; j < N; j++) {
+                if (e_row[i] == OZ_NONFINITE || f_col[j] == OZ_NONFINITE) {
+                    C[i + j * ldc] = NAN;
+                    continue;
+                }
                 __int128 S = 0;
                 for (int d = 2; d <= s + 1; d++) S += (__int128)G[(size_t)d * N + j] << (7 * (s + 1 - d));
-                double v = alpha * ldexp((double)S, e_row[i] + f_col[j] - 7 * (s + 1));
+                double v = alpha * oracle_round_scaled(S, e_row[i] + f_col[j] - 7 * (s + 1));
                 if (beta != 0.0) v = v + beta * C[i + j * ldc];
                 C[i + j * ldc] = v;
             }

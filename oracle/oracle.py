@@ -224,6 +224,8 @@ def _ozaki_sigs():
     L = lib()
     if getattr(L, "_oz_ready", False):
         return L
+    L.oracle_round_scaled_parts.restype = C.c_double
+    L.oracle_round_scaled_parts.argtypes = [C.c_int64, C.c_uint64, C.c_int]
     L.oracle_ozaki_split.restype = None
     L.oracle_ozaki_split.argtypes = [C.c_double, C.c_int, C.POINTER(C.c_int)]
     L.oracle_ozaki_exponents.restype = None
@@ -237,6 +239,22 @@ def _ozaki_sigs():
                                     C.POINTER(C.c_int64)]
     L._oz_ready = True
     return L
+
+
+# exponent marker of a row of A / column of B that holds a NaN or an infinity:
+# every C element of that row / column is NaN
+OZ_NONFINITE = 1 << 20
+
+
+def round_scaled(S: int, k: int) -> float:
+    """The integer S (|S| < 2^127) times 2^k, rounded once to the nearest double."""
+    S = int(S)
+    assert -(1 << 127) < S < (1 << 127)
+    u = S & ((1 << 128) - 1)
+    hi, lo = u >> 64, u & ((1 << 64) - 1)
+    if hi >= 1 << 63:
+        hi -= 1 << 64
+    return _ozaki_sigs().oracle_round_scaled_parts(hi, lo, int(k))
 
 
 def ozaki_split(x: float, s: int):

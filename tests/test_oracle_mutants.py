@@ -128,14 +128,14 @@ MUTANTS = [
      "(void)frexp(mu, &e);\n    return e;",
      "(void)frexp(mu, &e);\n    return e - 1;"),
     ("row maximum taken as its last element", C_SRC,
-     "for (int64_t l = 0; l < K; l++) { double v = fabs(A[i + l * lda]); if (v > mu) mu = v; }",
-     "for (int64_t l = 0; l < K; l++) { double v = fabs(A[i + l * lda]); mu = v; }"),
+     "else if (v > mu) mu = v;",
+     "else mu = v;"),
     ("dense GEMM: product and sum fused (FMA)", C_SRC,
      "s = s + x * y;",
      "s = fma(x, y, s);"),
     ("column maximum taken as its last element", C_SRC,
-     "for (int64_t l = 0; l < K; l++) { double v = fabs(B[l + j * ldb]); if (v > nu) nu = v; }",
-     "for (int64_t l = 0; l < K; l++) { double v = fabs(B[l + j * ldb]); nu = v; }"),
+     "else if (v > nu) nu = v;",
+     "else nu = v;"),
     ("level s + 1 dropped", C_SRC,
      "for (int u = 1; u + t <= s + 1; u++) {",
      "for (int u = 1; u + t <= s; u++) {"),
@@ -151,6 +151,18 @@ MUTANTS = [
     ("Ozaki: old C read when beta = 0", C_SRC,
      "if (beta != 0.0) v = v + beta * C[i + j * ldc];",
      "v = v + beta * C[i + j * ldc];"),
+    ("non-finite row of A not marked NaN", C_SRC,
+     "if (e_row[i] == OZ_NONFINITE || f_col[j] == OZ_NONFINITE) {",
+     "if (f_col[j] == OZ_NONFINITE) {"),
+    ("non-finite column of B not marked NaN", C_SRC,
+     "if (e_row[i] == OZ_NONFINITE || f_col[j] == OZ_NONFINITE) {",
+     "if (e_row[i] == OZ_NONFINITE) {"),
+    ("subnormal result rounded twice (53 bits, then at 2^-1074)", C_SRC,
+     "if (n - 1 + k < -1022) drop = -1074 - k;",
+     "if (0) drop = -1074 - k;"),
+    ("rounding tie broken away from zero", C_SRC,
+     "if (rem > half || (rem == half && (q & 1))) q += 1;",
+     "if (rem >= half) q += 1;"),
     # ---- Python helpers of the oracle
     ("densify: block placed at the transposed corner", PY_SRC,
      "D[ro[i]:ro[i] + m, co[j]:co[j] + n] = np.asarray(M.data[pos:pos + m * n]).reshape((m, n), order=\"F\")",

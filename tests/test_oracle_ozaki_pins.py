@@ -171,3 +171,125 @@ def test_recombination_is_exact_sum_rounded_once(s):
             exact = sum(Fraction(int(lv[d - 2][i][j])) * Fraction(2) ** (-7 * d) for d in range(2, s + 2))
             exact *= Fraction(2) ** (int(e[i]) + int(f[j]))
             assert Cd[i, j] == float(exact)
+
+
+def _exact_scaled(S, k):
+    """S * 2^k as Python rounds it (int / int and int -> float round to nearest, ties to even)."""
+    try:
+        return float(S << k) if k >= 0 else S / (1 << -k)
+    except OverflowError:
+        return math.copysign(math.inf, S)
+
+
+def _bits(x):
+    return np.array([x], np.float64).view(np.uint64)[0]
+
+
+def test_round_scaled_matches_exact_rationals():
+    rng = np.random.default_rng(58)
+    cases = []
+    for _ in range(3000):
+        n = int(rng.integers(1, 127))
+        S = int(rng.integers(1 << 30)) | (1 << (n - 1)) if n > 30 else int(rng.integers(1, 1 << n))
+        S = (S << max(0, n - 31)) | int(rng.integers(0, 1 << min(n, 62))) if n > 30 else S
+        S = S % (1 << 126) or 1
+        if rng.random() < 0.5:
+            S = -S
+        # k around the normal range, the subnormal range and overflow
+        lead = S.bit_length() - 1 if S > 0 else (-S).bit_length() - 1
+        k = int(rng.choice([rng.integers(-1200, 1100) - lead, -1022 - lead - rng.integers(0, 60),
+                            -1074 - lead + rng.integers(-3, 3), 1023 - lead + rng.integers(-1, 2)]))
+        cases.append((S, k))
+    # a tie created by rounding first to 53 bits and then again at the subnormal
+    # precision: rounded once, the remainder below the last kept bit (2^76 of S)
+    # is less than half of it, so the result is (2^23 + 1) 2^-1074
+    S_dr = (1 << 99) + (1 << 76) + ((1 << 75) - (1 << 46))
+    cases += [(S_dr, -1150), (-S_dr, -1150), (1, -1075), (3, -1075), (-1, -1076), (1, -1074),
+              ((1 << 53) - 1, 971), ((1 << 54) - 1, 970), (1 << 126, -2000), (5, 0), (0, 3)]
+    assert O.round_scaled(S_dr, -1150) == (2 ** 23 + 1) * 2.0 ** -1074
+    for S, k in cases:
+        got, want = O.round_scaled(S, k), _exact_scaled(S, k)
+        assert _bits(got) == _bits(want), (S, k, got, want)
+
+
+def _py_emulated_gemm(A, B, s):
+    """The integer-slice emulation on tiny inputs with Python integers and
+    fractions only: exponents from math.frexp of the line maxima, slices by
+    truncation of the exact scaled values, level sums t + u <= s + 1, the exact
+    sum S rounded once by Python's exact int / int division."""
+    M, K = A.shape
+    N = B.shape[1]
+    e = [math.frexp(max(abs(float(v)) for v in A[i])) [1] if np.any(A[i]) else 0 for i in range(M)]
+    f = [math.frexp(max(abs(float(v)) for v in B[:, j]))[1] if np.any(B[:, j]) else 0 for j in range(N)]
+
+    def slices(x, ex):
+        q = Fraction(float(x)) / Fraction(2) ** ex * (1 << (7 * s))
+        a = int(abs(q))                        # truncation toward zero
+        sg = -1 if q < 0 else 1
+        return [sg * ((a >> (7 * (s - t))) & 127) for t in range(1, s + 1)]
+
+    SA = [[slices(A[i, l], e[i]) for l in range(K)] for i in range(M)]
+    SB = [[slices(B[l, j], f[j]) for j in range(N)] for l in range(K)]
+    C = np.zeros((M, N))
+    for i in range(M):
+        for j in range(N):
+            S = 0
+            for d in range(2, s + 2):
+                G = sum(SA[i][l][t - 1] * SB[l][j][d - t - 1] for l in range(K) for t in range(1, d) if d - t <= s)
+                S += G << (7 * (s + 1 - d))
+            C[i, j] = _exact_scaled(S, e[i] + f[j] - 7 * (s + 1))
+    return C
+
+
+@pytest.mark.parametrize("scale_a,scale_b", [(0, 0), (-560, -480), (-540, -520), (-700, -362), (-600, -500),
+                                             (530, 500)])
+def test_emulation_against_python_integers(scale_a, scale_b):
+    # (0, 0): ordinary values; then results in the subnormal range (rounded at
+    # the bit of weight 2^-1074), below it (signed zeros) and beyond the
+    # largest double (infinities)
+    rng = np.random.default_rng(59 + abs(scale_a))
+    M, K, N, s = 3, 5, 4, 5
+    A = np.asfortranarray(rng.uniform(-1, 1, (M, K)) * 2.0 ** scale_a)
+    B = np.asfortranarray(rng.uniform(-1, 1, (K, N)) * 2.0 ** scale_b)
+    got = np.zeros((M, N), order="F")
+    O.ozaki_gemm(1.0, A, B, 0.0, got, s=s)
+    want = _py_emulated_gemm(A, B, s)
+    assert np.array_equal(got.view(np.uint64), want.view(np.uint64))
+    if -1074 < scale_a + scale_b < -1030:
+        assert np.any((got != 0) & (np.abs(got) < 2.0 ** -1022))   # the subnormal range is exercised
+    if scale_a + scale_b > 1024:
+        assert np.any(np.isinf(got))
+
+
+@pytest.mark.parametrize("bad", [np.nan, np.inf, -np.inf])
+def test_nonfinite_lines_give_nan(bad):
+    # a NaN or an infinity in row i of A (column j of B) makes C's row i
+    # (column j) NaN -- where IEEE FP64 gives a NaN or an infinity -- and leaves
+    # every other element as it is without that line
+    rng = np.random.default_rng(60)
+    M, K, N = 6, 7, 5
+    A = np.asfortranarray(rng.uniform(-1, 1, (M, K)))
+    B = np.asfortranarray(rng.uniform(-1, 1, (K, N)))
+    A[2, 3] = bad
+    B[4, 1] = bad
+    C0 = np.asfortranarray(rng.uniform(-1, 1, (M, N)))
+    C0[0, 4] = np.nan                                   # an old NaN propagates where beta reads it
+    for alpha, beta in ((1.0, 0.0), (0.5, 2.0), (0.0, 1.0)):
+        got = C0.copy(order="F")
+        O.ozaki_gemm(alpha, A, B, beta, got, s=7)
+        with np.errstate(invalid="ignore"):
+            ieee = A @ B
+        poisoned = ~np.isfinite(ieee)
+        assert poisoned[2].all() and poisoned[:, 1].all() and poisoned.sum() == N + M - 1
+        want_nan = poisoned | (np.isnan(C0) if beta != 0.0 else False)
+        assert np.array_equal(np.isnan(got), want_nan)
+        A0, B0 = A.copy(order="F"), B.copy(order="F")
+        A0[2, 3] = 0.0
+        B0[4, 1] = 0.0
+        clean = C0.copy(order="F")
+        O.ozaki_gemm(alpha, A0, B0, beta, clean, s=7)
+        keep = ~want_nan
+        assert np.array_equal(got[keep], clean[keep])
+    e, f = O.ozaki_exponents(A, B)
+    assert e[2] == O.OZ_NONFINITE and f[1] == O.OZ_NONFINITE
+    assert all(v != O.OZ_NONFINITE for q, v in enumerate(e) if q != 2)
