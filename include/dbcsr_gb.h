@@ -69,13 +69,14 @@ typedef void *(*dbcsr_alloc_fn)(size_t bytes, void *stream, void *ctx);
 typedef void (*dbcsr_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
 
 /* Execution path of dbcsr_multiply (Sec. II stacks vs Sec. III densification). */
-#define DBCSR_PATH_AUTO   0  /* dense path when op(A) and op(B) are 100% occupied, else stacks */
+#define DBCSR_PATH_AUTO   0  /* dense path when op(A) and op(B) are 100% occupied (FP32:
+                                always stacks); else stacks, except where the stack kernels
+                                do not apply: emulated FP64 with a block edge above 32 and
+                                TF32 take the dense path (Sec. II: blocks beyond the small
+                                kernels' range go to a GEMM) */
 #define DBCSR_PATH_STACKS 1  /* stacks of block products, batched small-GEMM kernels. FP64
                                 and FP32: any block size. Emulated FP64: block edges up
-                                to 32 (DBCSR_ERR_ARG above). TF32: none (DBCSR_ERR_ARG). So
-                                sparse operands with larger blocks (emulated) or in TF32
-                                need DBCSR_PATH_DENSE or DBCSR_PATH_HYBRID, chosen
-                                explicitly: AUTO does not switch on block size */
+                                to 32 (DBCSR_ERR_ARG above). TF32: none (DBCSR_ERR_ARG) */
 #define DBCSR_PATH_DENSE  2  /* densify, one GEMM, undensify (any occupancy; absent blocks = 0) */
 #define DBCSR_PATH_HYBRID 3  /* per panel of block rows of op(A): densified GEMM where the panel
                                 (and op(B)) is at least hybrid_fill_pct % occupied, stacks elsewhere
@@ -261,11 +262,26 @@ DBCSR_API int dbcsr_get_stacks(char transa, char transb, dbcsr_matrix A, dbcsr_m
  * call allocates nothing. Sizes whose scratch exceeds it (about
  * M = N = K = 1024 with 7 slices) return DBCSR_ERR_OVERFLOW with a message.
  * The first call on a device looks up the array's device address (once per
- * device); make that first call before any stream capture. All calls share
- * the array: calls whose work overlaps on the GPU race on it. */
+ * device); make that first call before any stream capture begins. Every call
+ * waits for its stream to finish the work before it returns. All calls share
+ * the array: calls whose work overlaps on the GPU (other streams, other host
+ * threads) race on it, so callers serialise them. */
 DBCSR_API int dbcsr_dgemm_emulated_noalloc(int64_t M, int64_t N, int64_t K, double alpha, const double *A,
                                            int64_t lda, const double *B, int64_t ldb, double beta, double *C,
                                            int64_t ldc, int slices, void *stream);
+
+/* Limit, in nanoseconds, of each bounded wait inside the tensor-core
+ * pipelines (the emulated-FP64 and TF32 GEMMs and the emulated stack kernel);
+ * ns <= 0 restores the default of 4 s. The paper has no counterpart: the
+ * kernels' stages hand work to each other through shared-memory barriers,
+ * and a wait that runs out makes the kernel stop every role, wait (always up
+ * to 4 s) for its own copies and tensor-core operations in flight, release
+ * its tensor memory and return; the call then fails with DBCSR_ERR_TIMEOUT
+ * and the library stays usable. A limit far below the pipeline's normal
+ * latency (a few microseconds) makes multiplies fail that way on purpose,
+ * which is what the failure tests use it for. Applies to calls made after it
+ * on any thread; not to dbcsr_dgemm_emulated_noalloc (fixed 4 s). */
+DBCSR_API int dbcsr_set_wait_limit(int64_t ns);
 
 /* Wait for all work the library queued on its stream. */
 DBCSR_API int dbcsr_sync(void);

@@ -16,6 +16,7 @@
 #include "dense.cuh"
 #include "emul.cuh"
 #include "smm.cuh"
+#include "smm_emul.cuh"
 #include "stackgen.cuh"
 
 namespace dbcsr {
@@ -1011,9 +1012,18 @@ extern "C" int dbcsr_multiply(char transa, char transb, double alpha, dbcsr_matr
     g_stats.n_products = np;
     int path = o.path;
     if (path == DBCSR_PATH_AUTO) {
+        // Sec. III: densify when both operands are dense. Sec. II: blocks beyond
+        // the small-matrix kernels' range go to a GEMM -- here the emulated
+        // stack kernels take edges up to 32, so larger blocks take the
+        // densified GEMM, as does TF32 (no stack kernel) on sparse operands.
         const bool a_full = A->nblks == (int64_t)A->nbr * A->nbc && A->nblks > 0;
         const bool b_full = B->nblks == (int64_t)B->nbr * B->nbc && B->nblks > 0;
-        path = (a_full && b_full && o.precision != DBCSR_PREC_FP32) ? DBCSR_PATH_DENSE : DBCSR_PATH_STACKS;
+        const int max_edge = std::max(std::max(A->max_rs, A->max_cs), std::max(B->max_rs, B->max_cs));
+        if (o.precision == DBCSR_PREC_FP32) path = DBCSR_PATH_STACKS;
+        else if (a_full && b_full) path = DBCSR_PATH_DENSE;
+        else if (o.precision == DBCSR_PREC_TF32) path = DBCSR_PATH_DENSE;
+        else if (o.precision == DBCSR_PREC_OZAKI && max_edge > EMUL_STACK_MAX_EDGE) path = DBCSR_PATH_DENSE;
+        else path = DBCSR_PATH_STACKS;
     }
     if (path == DBCSR_PATH_DENSE && o.precision == DBCSR_PREC_FP32)
         return fail(DBCSR_ERR_ARG, "multiply: FP32 runs on the stack path (the dense path offers TF32)");
@@ -1032,6 +1042,12 @@ extern "C" int dbcsr_multiply(char transa, char transb, double alpha, dbcsr_matr
     C->h_valid = false;
     C->t_valid = false;
     return rc;
+}
+
+extern "C" int dbcsr_set_wait_limit(int64_t ns) {
+    g_last_error.clear();
+    g_ctx.wait_ns = ns > 0 ? (uint64_t)ns : 4000000000ull;
+    return DBCSR_OK;
 }
 
 extern "C" int dbcsr_get_stacks(char transa, char transb, dbcsr_matrix A, dbcsr_matrix B, int stack_cap, int* out,

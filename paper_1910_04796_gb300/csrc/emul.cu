@@ -2,15 +2,18 @@
 // (Ozaki, Ogita, Oishi & Rump 2012, integer form) on the tensor cores.
 //
 //   1. exponents: e_i = frexp exponent of max_l |A(i,l)|, f_j likewise for
-//      the columns of B, so |A(i,l)| 2^-e_i < 1 and |B(l,j)| 2^-f_j < 1;
+//      the columns of B, so |A(i,l)| 2^-e_i < 1 and |B(l,j)| 2^-f_j < 1; a
+//      row or column holding a NaN or an infinity gets a marker instead and
+//      its C elements come out NaN;
 //   2. slices: sigma_t = the t-th 7-bit group of floor(|x| 2^(7s)) with the
 //      sign of x -- the same integers as s rounds of "truncate x 2^(7t),
 //      subtract", extracted here from the FP64 bit pattern with integer
 //      operations (exact, no FP64 arithmetic); stored as bf16 (exact);
 //   3. level sums G_d = sum_{t+u=d} S^A_t S^B_u for d = 2 .. s+1 on the
 //      tensor cores, exactly (tc_ozaki.cu);
-//   4. recombination in FP64: acc = sum_{d=s+1..2} G_d 2^(-7d) (one rounding
-//      per level, smallest first), C = alpha (acc 2^(e_i+f_j)) + beta C.
+//   4. recombination: the exact 128-bit S = sum_d G_d 2^(7(s+1-d)), and
+//      S 2^(e_i+f_j-7(s+1)) rounded once to FP64 (subnormal results too);
+//      C = alpha * that + beta C.
 // Steps 1, 2 and 4 are HBM-bound elementwise kernels; step 3 carries the work.
 #include <cuda_bf16.h>
 
@@ -69,10 +72,7 @@ __global__ void k_colmax_bits(int64_t K, const double* __restrict__ B, int64_t l
 __global__ void k_exponents(int64_t n, const unsigned long long* __restrict__ bits, int* __restrict__ e) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double mu = __longlong_as_double((long long)bits[i]);
-    int ex = 0;
-    if (mu != 0.0) frexp(mu, &ex);
-    e[i] = ex;
+    e[i] = emul::exponent_of_bits(bits[i]);
 }
 
 using emul::fixed_point;
@@ -136,7 +136,7 @@ __global__ void k_recombine(int64_t M, int64_t N, int s, int ksegs, const double
         for (int k = 0; k < ksegs; k++) g += (long long)ws[((int64_t)(d - 2) * ksegs + k) * stride + idx];
         S += (__int128)g << (7 * (s + 1 - d));
     }
-    const double x = emul::round_i128_scaled(S, e[i] + f[j] - 7 * (s + 1));
+    const double x = emul::recombined(S, e[i] + f[j], 7 * (s + 1));
     const BlasUpd bu(alpha, beta);
     C[i + j * ldc] = bu.old ? bu.update(x, C[i + j * ldc]) : bu.scale(x);
 }
@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(256) k_recombine_rm(int64_t M, int64_t N, int 
         }
         const __int128 Sx = (__int128)U * ((__int128)1 << (7 * (S - NU))) + V;
         const int64_t i = i0 + ty + 8 * c;
-        tile[ty + 8 * c][tx] = in[c] ? emul::round_i128_scaled(Sx, e[i] + fj - 7 * (S + 1)) : 0.0;
+        tile[ty + 8 * c][tx] = in[c] ? emul::recombined(Sx, e[i] + fj, 7 * (S + 1)) : 0.0;
     }
     __syncthreads();
 #pragma unroll
@@ -420,13 +420,12 @@ int oz_run(int64_t M, int64_t N, int64_t K, int64_t ldk, int s, const __nv_bfloa
     double* C = out.C;
     const int64_t ldc = out.ldc;
     // 128 x 256 tiles when the output is wide enough (fewer bytes moved per
-    // flop), else 128 x 128 tiles in clusters of two sharing the B tile
+    // flop), else 128 x 128 tiles
     const bool wide = N >= 256 && tc256_usable();
     const int tn = wide ? 256 : 128;
-    const int cm = wide ? 1 : tc_cluster_m(M);
     CUtensorMap tmA, tmB;
     DB_TRY(make_slice_tmap(&tmA, SA.p, ldk, M, s, 128, 2));
-    DB_TRY(make_slice_tmap(&tmB, SB.p, ldk, N, s, tn / cm, 2));
+    DB_TRY(make_slice_tmap(&tmB, SB.p, ldk, N, s, tn, 2));
     OzParams p{};
     p.chunk_blocks = OZ_CHUNK_BLOCKS;
     p.elem_bytes = 2;
@@ -442,6 +441,7 @@ int oz_run(int64_t M, int64_t N, int64_t K, int64_t ldk, int s, const __nv_bfloa
     if (p.units >= INT32_MAX) return fail(DBCSR_ERR_OVERFLOW, "emulated gemm: too many work units");
     p.ws_stride = M * N;
     p.err = ctx().d_flags;
+    p.wait_ns = ctx().wait_ns;
     DB_CUDA(cudaMemsetAsync(p.err, 0, sizeof(int), st));
     int h_err = 0;
     if (wide) {
@@ -469,7 +469,7 @@ int oz_run(int64_t M, int64_t N, int64_t K, int64_t ldk, int s, const __nv_bfloa
         DB_TRY(ws.alloc((size_t)s * p.ksegs * M * N));
         p.ws = ws.p;
         timer_kernel_begin();
-        DB_TRY(oz_gemm_launch(tmA, tmB, p, cm));
+        DB_TRY(oz_gemm_launch(tmA, tmB, p));
         timer_kernel_end();
         DB_CUDA(cudaMemcpyAsync(&h_err, p.err, sizeof(int), cudaMemcpyDeviceToHost, st));
         k_recombine<<<(unsigned)cdiv(M * N, 256), 256, 0, st>>>(M, N, s, p.ksegs, ws.p, p.ws_stride, e.p, f.p,
@@ -569,6 +569,7 @@ namespace dbcsr {
 namespace {
 
 constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(128) << 20;   // 128 MiB
+constexpr uint64_t NOALLOC_WAIT_NS = 4000000000ull;            // each pipeline wait gives up after 4 s
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
 constexpr int NOALLOC_MAX_DEVICES = 64;
@@ -691,6 +692,7 @@ int dgemm_ozaki_noalloc(int64_t M, int64_t N, int64_t K, double alpha, const dou
     p.ws = ws;
     p.ws_stride = M * N;
     p.err = err;
+    p.wait_ns = NOALLOC_WAIT_NS;
     DB_TRY(oz_gemm_launch_on(tmA, tmB, p, st, sms));
     k_recombine<<<(unsigned)cdiv(M * N, 256), 256, 0, st>>>(M, N, s, ksegs, ws, p.ws_stride, e, f, alpha, beta, C,
                                                            ldc);

@@ -44,8 +44,17 @@ __device__ __forceinline__ __nv_bfloat16 slice_bf16(long long q, int t, int s) {
     return __ushort_as_bfloat16((unsigned short)(__float_as_uint(fv) >> 16));
 }
 
-// frexp exponent of a magnitude given by its bit pattern (0 for zero)
+// Exponent marker of a line (row of op(A) / column of op(B)) that holds a NaN
+// or an infinity: the line has no finite maximum to scale by. Its slices come
+// out zero (the shift in fixed_point is far below -64) and every C element of
+// the line is NaN. Real exponents lie in [-1073, 1024], so a sum e_i + f_j
+// above NONFINITE_EXP / 2 means that one of the two lines is marked.
+constexpr int NONFINITE_EXP = 1 << 20;
+
+// frexp exponent of a magnitude given by its bit pattern (0 for zero;
+// NONFINITE_EXP for an infinity or a NaN, whose patterns are the largest)
 __device__ __forceinline__ int exponent_of_bits(unsigned long long bits) {
+    if (bits >= 0x7ff0000000000000ull) return NONFINITE_EXP;
     const double mu = __longlong_as_double((long long)bits);
     int ex = 0;
     if (mu != 0.0) frexp(mu, &ex);
@@ -56,24 +65,40 @@ __device__ __forceinline__ unsigned long long abs_bits(double x) {
     return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
 }
 
-// mant * 2^ex * 2^k with the sign, for results outside the normal range. A
-// call of its own: inlined, the compiler would turn the rare branch into
-// predicated FP64 instructions that occupy the FP64 pipe for every element.
-static __device__ __noinline__ double scaled_outside_normal(unsigned long long mant, int ex, int k, bool neg) {
-    const double r = ldexp((double)mant, ex);   // exact: mant < 2^53
-    return ldexp(neg ? -r : r, k);
+// |S| 2^k with the sign for a result below the normal range: rounded once, to
+// nearest with ties to even, at the bit of weight 2^-1074 (bit d = -1074 - k
+// of |S|, d > msb - 52; for d <= 0 every bit is kept and |S| < 2^52). The kept
+// integer q is at most 2^52, so it is the double's bit pattern as it stands
+// (q = 2^52 is the smallest normal). A call of its own: inlined, the rare
+// branch would cost every element registers.
+static __device__ __noinline__ double round_subnormal(unsigned long long hi, unsigned long long lo, int k,
+                                                      bool neg) {
+    const int d = -1074 - k;
+    unsigned long long q = 0;
+    if (d <= 0) {
+        q = lo << (-d);
+    } else if (d < 128) {
+        const unsigned __int128 a = ((unsigned __int128)hi << 64) | lo;
+        q = (unsigned long long)(a >> d);
+        const unsigned __int128 rem = a - ((unsigned __int128)q << d);
+        const unsigned __int128 half = (unsigned __int128)1 << (d - 1);
+        if (rem > half || (rem == half && (q & 1ull))) q += 1;
+    }   // d >= 128: |S| < 2^127 <= half of the last bit: zero
+    return __longlong_as_double((long long)(((unsigned long long)neg << 63) | q));
 }
 
 // Recombination of the level sums: S = sum_d G_d 2^(7(s+1-d)) is an exact
-// 128-bit integer; the result is S rounded once to FP64 (to nearest, ties to
-// even) and multiplied by 2^k exactly -- the same as ldexp((double)S, k).
-// Integer operations only, except ldexp outside the normal range.
+// 128-bit integer; the result is the real number S 2^k rounded once to FP64
+// (to nearest, ties to even): 53 significant bits when it is normal, down to
+// the bit of weight 2^-1074 when it is subnormal, +-infinity beyond the
+// largest double. Integer operations only.
 __device__ __forceinline__ double round_i128_scaled(__int128 S, int k) {
     if (S == 0) return 0.0;
     const bool neg = S < 0;
     const unsigned __int128 a = neg ? (unsigned __int128)(-S) : (unsigned __int128)S;
     const unsigned long long hi = (unsigned long long)(a >> 64), lo = (unsigned long long)a;
     const int msb = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);   // leading one
+    if (msb + k < -1022) return round_subnormal(hi, lo, k, neg);
     unsigned long long mant;   // significand in [2^52, 2^53)
     int ex;                    // |S| rounded = mant * 2^ex
     if (msb <= 52) {
@@ -113,13 +138,18 @@ __device__ __forceinline__ double round_i128_scaled(__int128 S, int k) {
             }
         }
     }
-    const int E = ex + k + 52;   // result = mant / 2^52 * 2^E
-    if (E >= -1022 && E <= 1023) {
-        const unsigned long long bits = ((unsigned long long)neg << 63) |
-                                        ((unsigned long long)(E + 1023) << 52) | (mant & 0xfffffffffffffull);
-        return __longlong_as_double((long long)bits);
-    }
-    return scaled_outside_normal(mant, ex, k, neg);
+    const int E = ex + k + 52;   // result = mant / 2^52 * 2^E, E >= -1022 here
+    if (E > 1023) return __longlong_as_double((long long)(((unsigned long long)neg << 63) | 0x7ff0000000000000ull));
+    const unsigned long long bits = ((unsigned long long)neg << 63) | ((unsigned long long)(E + 1023) << 52) |
+                                    (mant & 0xfffffffffffffull);
+    return __longlong_as_double((long long)bits);
+}
+
+// The recombined value of one C element: S 2^(ef - shift) rounded once, with
+// ef = e_i + f_j; NaN when either line holds a non-finite value.
+__device__ __forceinline__ double recombined(__int128 S, int ef, int shift) {
+    if (ef > NONFINITE_EXP / 2) return __longlong_as_double(0x7ff8000000000000ll);
+    return round_i128_scaled(S, ef - shift);
 }
 
 }  // namespace emul

@@ -61,6 +61,8 @@ struct Context {
     // device scratch reused across calls (error flag, work counters)
     int* d_flags = nullptr;
     int64_t* d_counters = nullptr;
+    // limit of each bounded wait in the tensor-core pipelines (dbcsr_set_wait_limit)
+    uint64_t wait_ns = 4000000000ull;
 };
 Context& ctx();
 int ensure_device();

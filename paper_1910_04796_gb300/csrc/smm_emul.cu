@@ -31,7 +31,7 @@ namespace dbcsr {
 namespace {
 
 constexpr int SE_THREADS = 128;
-constexpr int SE_MAXB = 32;    // largest block edge on this path
+constexpr int SE_MAXB = EMUL_STACK_MAX_EDGE;    // largest block edge on this path
 constexpr int SE_RS = 40;      // shared-memory row stride (bf16): 32 + 8, conflict-free fragments
 
 __host__ __device__ inline int ru16(int x) { return (x + 15) & ~15; }
@@ -294,8 +294,7 @@ __global__ void __launch_bounds__(SE_THREADS) k_smm_emul(SeArgs a) {
                     __int128 Sx = 0;   // exact sum of the level sums, each shifted to its weight
 #pragma unroll
                     for (int d = 0; d < S; d++) Sx += (__int128)gi[d][nt][r] << (7 * (S - 1 - d));
-                    const double x =
-                        emul::round_i128_scaled(Sx, a.e[rbase + row] + a.f[cbase + colm] - 7 * (S + 1));
+                    const double x = emul::recombined(Sx, a.e[rbase + row] + a.f[cbase + colm], 7 * (S + 1));
                     const int64_t eidx = (int64_t)colm * m + row;
                     cout[eidx] = cold ? bu.update(x, cold[eidx]) : bu.scale(x);
                 }

@@ -7,6 +7,10 @@
 
 namespace dbcsr {
 
+// largest block edge the emulated stack kernels take (blocks are padded to 32
+// x 32 on the tcgen05 kernel, to multiples of 16 up to 32 on the mma.sync one)
+constexpr int EMUL_STACK_MAX_EDGE = 32;
+
 // One matrix seen through op(): stored block b, element (x, l) of its op()
 // "row-like" view is data[off[b] + x*xs + l*ls]: x indexes op(A)'s rows (or
 // op(B)'s columns), l the inner dimension.

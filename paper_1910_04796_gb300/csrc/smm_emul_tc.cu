@@ -47,7 +47,9 @@
 //     exactly, round, scale and store -- while the drain warps fill the other
 //     of the two level-sum buffers with the next C block.
 // int32 level sums are exact while products * s * 32 * 127^2 < 2^31 (checked
-// on the host). Every wait is bounded (4 s): on expiry the kernel sets the
+// on the host). Every pipeline wait is bounded (TcArgs::wait_ns, 4 s unless a
+// caller set another limit; the clean-up waits before exit always allow 4 s):
+// on expiry the kernel sets the
 // error flag, the other roles see the abort flag, every role leaves its loop
 // and TMEM is freed.
 #include <cuda_bf16.h>
@@ -70,7 +72,7 @@ constexpr int TC_SLOT = 2048;                 // one 32 x 32 bf16 slice
 constexpr int TC_SMEM_CAP = 232448;           // 227 KB of shared memory per CTA
 constexpr int TC_SMEM_MIN = 120 * 1024;       // one CTA per SM: it allocates all 512 TMEM columns
 constexpr int TC_ACC_COLS = 256;              // TMEM columns of one accumulator buffer (two buffers)
-constexpr uint64_t TC_WAIT_NS = 4000000000ull;
+constexpr uint64_t TC_DRAIN_NS = 4000000000ull;   // clean-up waits before the CTA exits
 // C blocks are visited tile by tile: the CTAs working at the same time share
 // the tile's A block rows and B block columns, which stay in L2
 constexpr int TC_TILE = 32;
@@ -132,6 +134,7 @@ struct TcArgs {
     const double* Cold;
     double alpha, beta;
     int* err;
+    uint64_t wait_ns;           // limit of each pipeline wait (ns on the global timer)
 };
 
 // Slices of every stored block in the operand layout above, zero-padded to
@@ -214,8 +217,9 @@ __device__ __forceinline__ longlong2 sched_range(const TcArgs& a, int64_t q) {
 }
 
 // all lanes of the warp agree: the wait succeeded and no role aborted
-__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
-    bool ok = !*abort_flag && ptx::mbar_wait_bounded(bar, parity, TC_WAIT_NS);
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                          uint64_t wait_ns) {
+    bool ok = !*abort_flag && ptx::mbar_wait_bounded(bar, parity, wait_ns);
     return __all_sync(0xffffffffu, ok);
 }
 
@@ -286,7 +290,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_smm_emul_tc(TcArgs a) {
                     const int st = (int)(it % G::NST);
                     const uint32_t ph = (uint32_t)((it / G::NST) & 1);
                     const int2 pr = a.prod[p];
-                    if (*abort_flag || !ptx::mbar_wait_bounded(&empty[st], ph ^ 1u, TC_WAIT_NS)) {
+                    if (*abort_flag || !ptx::mbar_wait_bounded(&empty[st], ph ^ 1u, a.wait_ns)) {
                         if (!*abort_flag) on_timeout();
                         ok = false;
                         break;
@@ -305,7 +309,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_smm_emul_tc(TcArgs a) {
             // no copy may still be in flight when the CTA exits
             const int64_t first = it > G::NST ? it - G::NST : 0;
             for (int64_t q = first; q < it; q++)
-                if (!ptx::mbar_wait_bounded(&full[q % G::NST], (uint32_t)((q / G::NST) & 1), TC_WAIT_NS)) {
+                if (!ptx::mbar_wait_bounded(&full[q % G::NST], (uint32_t)((q / G::NST) & 1), TC_DRAIN_NS)) {
                     on_timeout();
                     break;
                 }
@@ -323,7 +327,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_smm_emul_tc(TcArgs a) {
                 for (int64_t c0 = cur.x; c0 < cur.y && ok; c0 += G::CHUNK, ci++) {
                     const int tb = (int)(ci & 1);
                     if (*abort_flag ||
-                        !ptx::mbar_wait_bounded(&tempty[tb], (uint32_t)(((ci >> 1) & 1) ^ 1), TC_WAIT_NS)) {
+                        !ptx::mbar_wait_bounded(&tempty[tb], (uint32_t)(((ci >> 1) & 1) ^ 1), a.wait_ns)) {
                         if (!*abort_flag) on_timeout();
                         ok = false;
                         break;
@@ -334,7 +338,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_smm_emul_tc(TcArgs a) {
                     for (int64_t p = c0; p < c1; p++, it++) {
                         const int st = (int)(it % G::NST);
                         const uint32_t ph = (uint32_t)((it / G::NST) & 1);
-                        if (*abort_flag || !ptx::mbar_wait_bounded(&full[st], ph, TC_WAIT_NS)) {
+                        if (*abort_flag || !ptx::mbar_wait_bounded(&full[st], ph, a.wait_ns)) {
                             if (!*abort_flag) on_timeout();
                             ok = false;
                             break;
@@ -360,7 +364,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_smm_emul_tc(TcArgs a) {
                 }
             }
             ptx::mma_commit(drain);
-            if (!ptx::mbar_wait_bounded(drain, 0, TC_WAIT_NS)) on_timeout();
+            if (!ptx::mbar_wait_bounded(drain, 0, TC_DRAIN_NS)) on_timeout();
         }
     } else if (warp < 2 + TC_DRAIN) {
         // ------------------------------------------------------------- drain
@@ -377,7 +381,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_smm_emul_tc(TcArgs a) {
         for (int64_t seq = blockIdx.x; seq < a.nC && ok; seq += gridDim.x, cbi++) {
             const longlong2 cur = sched_range(a, seq);
             const int buf = (int)(cbi & 1);
-            if (!warp_wait(&lfree[buf], (uint32_t)(((cbi >> 1) & 1) ^ 1), abort_flag)) {
+            if (!warp_wait(&lfree[buf], (uint32_t)(((cbi >> 1) & 1) ^ 1), abort_flag, a.wait_ns)) {
                 if (!*abort_flag) on_timeout();
                 ok = false;
                 break;
@@ -385,7 +389,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_smm_emul_tc(TcArgs a) {
             int* ls = LS + buf * G::LSBUF + lane * TC_LROW;   // level 0, row lane
             for (int64_t c0 = cur.x; c0 < cur.y; c0 += G::CHUNK, ci++) {
                 const int tb = (int)(ci & 1);
-                if (!warp_wait(&tfull[tb], (uint32_t)((ci >> 1) & 1), abort_flag)) {
+                if (!warp_wait(&tfull[tb], (uint32_t)((ci >> 1) & 1), abort_flag, a.wait_ns)) {
                     if (!*abort_flag) on_timeout();
                     ok = false;
                     break;
@@ -438,7 +442,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_smm_emul_tc(TcArgs a) {
                 oldv[k] = (in && cur.old_off >= 0) ? a.Cold[cur.old_off + e] : 0.0;
             }
             const int buf = (int)(cbi & 1);
-            if (!warp_wait(&lfull[buf], (uint32_t)((cbi >> 1) & 1), abort_flag)) {
+            if (!warp_wait(&lfull[buf], (uint32_t)((cbi >> 1) & 1), abort_flag, a.wait_ns)) {
                 if (!*abort_flag) on_timeout();
                 ok = false;
                 break;
@@ -472,7 +476,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_smm_emul_tc(TcArgs a) {
 #pragma unroll
                 for (int d = NU; d < S; d++) V = V * 128 + lv[d][k];
                 const __int128 Sx = (__int128)U * ((__int128)1 << (7 * (S - NU))) + V;
-                const double x = emul::round_i128_scaled(Sx, ex[k] - 7 * (S + 1));
+                const double x = emul::recombined(Sx, ex[k], 7 * (S + 1));
                 cout[e] = cur.old_off >= 0 ? bu.update(x, oldv[k]) : bu.scale(x);
             }
         }
@@ -567,6 +571,7 @@ int smm_emul_tc(const SmmArgs& g, dbcsr_matrix_s* A, bool ta, dbcsr_matrix_s* B,
     a.alpha = g.alpha;
     a.beta = g.beta;
     a.err = ctx().d_flags;
+    a.wait_ns = ctx().wait_ns;
     DB_CUDA(cudaMemsetAsync(a.err, 0, sizeof(int), st));
     const int grid = (int)std::min<int64_t>(nsel, ctx().num_sms);
     int rc;

@@ -25,20 +25,18 @@ struct OzParams {
     int64_t ldc;
     double alpha, beta;
     int* err;             // set to 1 on a timed-out wait
+    uint64_t wait_ns;     // limit of each pipeline wait (ns on the global timer)
 };
 
 int make_slice_tmap(CUtensorMap* map, const void* base, int64_t ldk, int64_t rows, int slices, int box_rows,
                     int elem_bytes);
-// CTAs per cluster along M for an M-row output (2: the B tile is multicast,
-// so tmB's box holds 128 / 2 rows)
-int tc_cluster_m(int64_t M);
-// slice GEMMs (bf16, 128 x 128 tiles) on the library stream
-int oz_gemm_launch(const CUtensorMap& tmA, const CUtensorMap& tmB, const OzParams& p, int cluster_m);
-// the same on an explicit stream and SM count, no clusters (tmB box 128 rows)
+// slice GEMMs (bf16, 128 x 128 tiles; tmA and tmB boxes of 128 rows) on the library stream
+int oz_gemm_launch(const CUtensorMap& tmA, const CUtensorMap& tmB, const OzParams& p);
+// the same on an explicit stream and SM count
 int oz_gemm_launch_on(const CUtensorMap& tmA, const CUtensorMap& tmB, const OzParams& p, cudaStream_t st,
                       int num_sms);
-// TF32 GEMM writing C directly
-int tf32_gemm_launch(const CUtensorMap& tmA, const CUtensorMap& tmB, const OzParams& p, int cluster_m);
+// TF32 GEMM writing C directly (128 x 128 tiles)
+int tf32_gemm_launch(const CUtensorMap& tmA, const CUtensorMap& tmB, const OzParams& p);
 
 // 128 x 256 tiles (tc_gemm256.cu): usable when its compiled register budget
 // matches its warp-group register split; tmB's box then holds 256 rows.

@@ -16,7 +16,8 @@
 // Register budget: launched with 384 threads x 168 registers = 64 512;
 // 128 x 56 + 256 x 224 = 64 512. The host checks the compiled register count
 // before launching (a larger split would make setmaxnreg.inc wait forever).
-// Every mbarrier wait is bounded as in k_tc_gemm.
+// Every mbarrier wait is bounded as in k_tc_gemm (pipeline waits by
+// OzParams::wait_ns, clean-up waits by a fixed 4 s).
 #include <cuda.h>
 
 #include "internal.cuh"
@@ -37,7 +38,7 @@ constexpr int W_LAUNCH_REGS = 168;               // 65536 / 384, rounded down to
 constexpr int W_REGS_CTRL = 56, W_REGS_EPI = 224;
 static_assert(128 * W_REGS_CTRL + 256 * W_REGS_EPI <= W_THREADS * W_LAUNCH_REGS, "register split exceeds launch");
 constexpr int W_SMEM = W_STAGES * (W_STAGE_A + W_STAGE_B) + 1024 + 256;
-constexpr uint64_t W_WAIT_NS = 4000000000ull;
+constexpr uint64_t W_DRAIN_NS = 4000000000ull;   // clean-up waits before the CTA exits
 constexpr int W_GROUP_M = 16;
 
 template <int MODE>
@@ -138,7 +139,7 @@ __global__ void __launch_bounds__(W_THREADS, 1)
                     for (int kb = kb0; kb < kb1; kb++, it++) {
                         const int st = (int)(it % W_STAGES);
                         const uint32_t ph = (uint32_t)((it / W_STAGES) & 1);
-                        if (*abort_flag || !ptx::mbar_wait_bounded(&empty[st], ph ^ 1u, W_WAIT_NS)) {
+                        if (*abort_flag || !ptx::mbar_wait_bounded(&empty[st], ph ^ 1u, p.wait_ns)) {
                             if (!*abort_flag) on_timeout();
                             ok = false;
                             break;
@@ -150,7 +151,7 @@ __global__ void __launch_bounds__(W_THREADS, 1)
             }
             const int64_t first = it > W_STAGES ? it - W_STAGES : 0;
             for (int64_t q = first; q < it; q++)
-                if (!ptx::mbar_wait_bounded(&full[q % W_STAGES], (uint32_t)((q / W_STAGES) & 1), W_WAIT_NS)) {
+                if (!ptx::mbar_wait_bounded(&full[q % W_STAGES], (uint32_t)((q / W_STAGES) & 1), W_DRAIN_NS)) {
                     on_timeout();
                     break;
                 }
@@ -167,7 +168,7 @@ __global__ void __launch_bounds__(W_THREADS, 1)
                     for (int c = kb0; c < kb1 && ok; c += p.chunk_blocks, ci++) {
                         const int buf = (int)(ci & 1);
                         const uint32_t aph = (uint32_t)((ci >> 1) & 1);
-                        if (*abort_flag || !ptx::mbar_wait_bounded(&tempty[buf], aph ^ 1u, W_WAIT_NS)) {
+                        if (*abort_flag || !ptx::mbar_wait_bounded(&tempty[buf], aph ^ 1u, p.wait_ns)) {
                             if (!*abort_flag) on_timeout();
                             ok = false;
                             break;
@@ -178,7 +179,7 @@ __global__ void __launch_bounds__(W_THREADS, 1)
                         for (int kb = c; kb < ce; kb++, it++) {
                             const int st = (int)(it % W_STAGES);
                             const uint32_t ph = (uint32_t)((it / W_STAGES) & 1);
-                            if (*abort_flag || !ptx::mbar_wait_bounded(&full[st], ph, W_WAIT_NS)) {
+                            if (*abort_flag || !ptx::mbar_wait_bounded(&full[st], ph, p.wait_ns)) {
                                 if (!*abort_flag) on_timeout();
                                 ok = false;
                                 break;
@@ -196,7 +197,7 @@ __global__ void __launch_bounds__(W_THREADS, 1)
                     }
             }
             ptx::mma_commit(drain);
-            if (!ptx::mbar_wait_bounded(drain, 0, W_WAIT_NS)) on_timeout();
+            if (!ptx::mbar_wait_bounded(drain, 0, W_DRAIN_NS)) on_timeout();
         }
     } else {
         asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(W_REGS_EPI));
@@ -224,7 +225,7 @@ __global__ void __launch_bounds__(W_THREADS, 1)
             for (int ch = 0; ch < nchunks; ch++, ci++) {
                 const int buf = (int)(ci & 1);
                 const uint32_t aph = (uint32_t)((ci >> 1) & 1);
-                if (*abort_flag || !ptx::mbar_wait_bounded(&tfull[buf], aph, W_WAIT_NS)) {
+                if (*abort_flag || !ptx::mbar_wait_bounded(&tfull[buf], aph, p.wait_ns)) {
                     if (!*abort_flag) on_timeout();
                     ok = false;
                     break;

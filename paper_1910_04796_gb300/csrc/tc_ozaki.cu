@@ -22,9 +22,11 @@
 //   warp 1      TMEM allocator; lane 0 issues tcgen05.mma (4 per stage) into
 //               one of two TMEM accumulators and commits to mbarriers
 //   warps 2..5  epilogue: tcgen05.ld, convert, accumulate / store
-// Every mbarrier wait is bounded (4 s on the global timer); on a timeout the
+// Every mbarrier wait of the pipeline is bounded (OzParams::wait_ns on the
+// global timer, 4 s unless a caller set another limit); on a timeout the
 // kernel records an error flag, unwinds all roles, drains its TMA loads and
-// MMAs, frees TMEM and returns -- the host reports DBCSR_ERR_TIMEOUT.
+// MMAs (those clean-up waits always allow 4 s), frees TMEM and returns -- the
+// host reports DBCSR_ERR_TIMEOUT. Each CTA loads its own A and B tiles.
 #include <cuda.h>
 
 #include "internal.cuh"
@@ -41,7 +43,7 @@ constexpr int MODE_TF32 = 1;
 constexpr int TC_TM = 128;
 constexpr int TC_TN = 128;
 constexpr int TC_ROW_BYTES = 128;     // one 128-byte swizzle row of K per tile row
-constexpr uint64_t TC_WAIT_NS = 4000000000ull;
+constexpr uint64_t TC_DRAIN_NS = 4000000000ull;   // clean-up waits before the CTA exits
 constexpr int TC_GROUP_M = 16;        // tile rasterisation group (L2 reuse)
 
 struct TcCfg {
@@ -73,14 +75,10 @@ struct ModeTraits<MODE_TF32> {
     }
 };
 
-// Work unit u -> (tile row, tile column, K segment, level). With clusters of CM
-// CTAs along M, a unit covers CM vertically adjacent tiles: CTA `rank` of the
-// cluster takes tile row tm * CM + rank, and all CTAs of a cluster walk the
-// same unit sequence (same tile column, level and K range, hence the same
-// B tile, which they share through multicast).
-__device__ __forceinline__ void unit_coords(int64_t u, const OzParams& p, int cm, int rank, int& tm, int& tn,
-                                            int& kseg, int& li) {
-    const int tiles_mc = (p.tiles_m + cm - 1) / cm;
+// Work unit u -> (tile row, tile column, K segment, level): level-major, and
+// within a level the tiles in groups of TC_GROUP_M tile rows.
+__device__ __forceinline__ void unit_coords(int64_t u, const OzParams& p, int& tm, int& tn, int& kseg, int& li) {
+    const int tiles_mc = p.tiles_m;
     const int64_t tiles = (int64_t)tiles_mc * p.tiles_n;
     int64_t x = u % tiles;
     int64_t r = u / tiles;
@@ -92,18 +90,17 @@ __device__ __forceinline__ void unit_coords(int64_t u, const OzParams& p, int cm
     const int first_m = (int)(g * TC_GROUP_M);
     const int gm = min(TC_GROUP_M, tiles_mc - first_m);
     const int64_t xi = x - g * per_group;
-    tm = (first_m + (int)(xi % gm)) * cm + rank;
+    tm = first_m + (int)(xi % gm);
     tn = (int)(xi / gm);
 }
 
-template <int MODE, int CM>
+template <int MODE>
 __global__ void __launch_bounds__(TcCfg::THREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, OzParams p) {
     using Cfg = TcCfg;
     using Tr = ModeTraits<MODE>;
-    const int rank = (CM > 1) ? (int)ptx::cluster_ctarank() : 0;
-    const int64_t cl_id = blockIdx.x / CM, n_cl = gridDim.x / CM;
-    const uint16_t cl_mask = (uint16_t)((1u << CM) - 1u);
+    const int64_t cl_id = blockIdx.x, n_cl = gridDim.x;
+    const uint64_t wait_ns = p.wait_ns;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* sA = smem;
@@ -120,7 +117,7 @@ __global__ void __launch_bounds__(TcCfg::THREADS, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < Cfg::STAGES; s++) {
             ptx::mbar_init(&full[s], 1);
-            ptx::mbar_init(&empty[s], CM);   // released by the MMA of every CTA sharing the stage
+            ptx::mbar_init(&empty[s], 1);
         }
         for (int b = 0; b < 2; b++) {
             ptx::mbar_init(&tfull[b], 1);
@@ -140,7 +137,6 @@ __global__ void __launch_bounds__(TcCfg::THREADS, 1)
     }
     ptx::tc_fence_before();
     __syncthreads();
-    if (CM > 1) ptx::cluster_sync();   // peers' barriers initialised before any multicast
     ptx::tc_fence_after();
     const uint32_t tmem = *tmem_holder;
     const int kelems = TC_ROW_BYTES / p.elem_bytes;   // K elements per k-block
@@ -157,7 +153,7 @@ __global__ void __launch_bounds__(TcCfg::THREADS, 1)
             bool ok = true;
             for (int64_t u = cl_id; u < p.units && ok; u += n_cl) {
                 int tm, tn, kseg, li;
-                unit_coords(u, p, CM, rank, tm, tn, kseg, li);
+                unit_coords(u, p, tm, tn, kseg, li);
                 const int d = li + 2;
                 const int kb0 = kseg * p.kseg_blocks;
                 const int kb1 = min(kb0 + p.kseg_blocks, p.kblocks);
@@ -165,23 +161,14 @@ __global__ void __launch_bounds__(TcCfg::THREADS, 1)
                     for (int kb = kb0; kb < kb1; kb++, it++) {
                         const int st = (int)(it % Cfg::STAGES);
                         const uint32_t ph = (uint32_t)((it / Cfg::STAGES) & 1);
-                        if (*abort_flag || !ptx::mbar_wait_bounded(&empty[st], ph ^ 1u, TC_WAIT_NS)) {
+                        if (*abort_flag || !ptx::mbar_wait_bounded(&empty[st], ph ^ 1u, wait_ns)) {
                             if (!*abort_flag) on_timeout();
                             ok = false;
                             break;
                         }
                         ptx::mbar_arrive_expect_tx(&full[st], Cfg::STAGE_A + Cfg::STAGE_B);
                         ptx::tma_load_3d(sA + st * Cfg::STAGE_A, &tmA, &full[st], kb * kelems, tm * TC_TM, t - 1);
-                        if (CM == 1) {
-                            ptx::tma_load_3d(sB + st * Cfg::STAGE_B, &tmB, &full[st], kb * kelems, tn * TC_TN,
-                                             d - t - 1);
-                        } else {
-                            // this CTA's share of the common B tile, written into every CTA of the cluster
-                            const int rows = TC_TN / CM;
-                            ptx::tma_load_3d_multicast(sB + st * Cfg::STAGE_B + rank * rows * TC_ROW_BYTES, &tmB,
-                                                       &full[st], kb * kelems, tn * TC_TN + rank * rows, d - t - 1,
-                                                       cl_mask);
-                        }
+                        ptx::tma_load_3d(sB + st * Cfg::STAGE_B, &tmB, &full[st], kb * kelems, tn * TC_TN, d - t - 1);
                     }
                 }
             }
@@ -189,7 +176,7 @@ __global__ void __launch_bounds__(TcCfg::THREADS, 1)
             const int64_t first = it > Cfg::STAGES ? it - Cfg::STAGES : 0;
             for (int64_t q = first; q < it; q++) {
                 if (!ptx::mbar_wait_bounded(&full[q % Cfg::STAGES], (uint32_t)((q / Cfg::STAGES) & 1),
-                                            TC_WAIT_NS)) {
+                                            TC_DRAIN_NS)) {
                     on_timeout();
                     break;
                 }
@@ -202,7 +189,7 @@ __global__ void __launch_bounds__(TcCfg::THREADS, 1)
             bool ok = true;
             for (int64_t u = cl_id; u < p.units && ok; u += n_cl) {
                 int tm, tn, kseg, li;
-                unit_coords(u, p, CM, rank, tm, tn, kseg, li);
+                unit_coords(u, p, tm, tn, kseg, li);
                 const int d = li + 2;
                 const int kb0 = kseg * p.kseg_blocks;
                 const int kb1 = min(kb0 + p.kseg_blocks, p.kblocks);
@@ -210,7 +197,7 @@ __global__ void __launch_bounds__(TcCfg::THREADS, 1)
                     for (int c = kb0; c < kb1 && ok; c += p.chunk_blocks, ci++) {
                         const int buf = (int)(ci & 1);
                         const uint32_t aph = (uint32_t)((ci >> 1) & 1);
-                        if (*abort_flag || !ptx::mbar_wait_bounded(&tempty[buf], aph ^ 1u, TC_WAIT_NS)) {
+                        if (*abort_flag || !ptx::mbar_wait_bounded(&tempty[buf], aph ^ 1u, wait_ns)) {
                             if (!*abort_flag) on_timeout();
                             ok = false;
                             break;
@@ -221,7 +208,7 @@ __global__ void __launch_bounds__(TcCfg::THREADS, 1)
                         for (int kb = c; kb < ce; kb++, it++) {
                             const int st = (int)(it % Cfg::STAGES);
                             const uint32_t ph = (uint32_t)((it / Cfg::STAGES) & 1);
-                            if (*abort_flag || !ptx::mbar_wait_bounded(&full[st], ph, TC_WAIT_NS)) {
+                            if (*abort_flag || !ptx::mbar_wait_bounded(&full[st], ph, wait_ns)) {
                                 if (!*abort_flag) on_timeout();
                                 ok = false;
                                 break;
@@ -235,9 +222,7 @@ __global__ void __launch_bounds__(TcCfg::THREADS, 1)
                                 Tr::mma(dt, ad + (uint64_t)((kk * 32) >> 4), bd + (uint64_t)((kk * 32) >> 4),
                                         (kb > c || kk > 0) ? 1u : 0u);
                             }
-                            // the stage is free once every CTA that shares it has consumed it
-                            if (CM == 1) ptx::mma_commit(&empty[st]);
-                            else ptx::mma_commit_multicast(&empty[st], cl_mask);
+                            ptx::mma_commit(&empty[st]);
                         }
                         if (ok) ptx::mma_commit(&tfull[buf]);
                     }
@@ -245,7 +230,7 @@ __global__ void __launch_bounds__(TcCfg::THREADS, 1)
             }
             // every issued MMA must be complete before TMEM is released
             ptx::mma_commit(drain);
-            if (!ptx::mbar_wait_bounded(drain, 0, TC_WAIT_NS)) on_timeout();
+            if (!ptx::mbar_wait_bounded(drain, 0, TC_DRAIN_NS)) on_timeout();
         }
     } else {
         // --------------------------------------------------------- epilogue
@@ -257,7 +242,7 @@ __global__ void __launch_bounds__(TcCfg::THREADS, 1)
         bool ok = true;
         for (int64_t u = cl_id; u < p.units && ok; u += n_cl) {
             int tm, tn, kseg, li;
-            unit_coords(u, p, CM, rank, tm, tn, kseg, li);
+            unit_coords(u, p, tm, tn, kseg, li);
             const int d = li + 2;
             const int kb0 = kseg * p.kseg_blocks;
             const int kb1 = min(kb0 + p.kseg_blocks, p.kblocks);
@@ -267,7 +252,7 @@ __global__ void __launch_bounds__(TcCfg::THREADS, 1)
             for (int ch = 0; ch < nchunks; ch++, ci++) {
                 const int buf = (int)(ci & 1);
                 const uint32_t aph = (uint32_t)((ci >> 1) & 1);
-                if (*abort_flag || !ptx::mbar_wait_bounded(&tfull[buf], aph, TC_WAIT_NS)) {
+                if (*abort_flag || !ptx::mbar_wait_bounded(&tfull[buf], aph, wait_ns)) {
                     if (!*abort_flag) on_timeout();
                     ok = false;
                     break;
@@ -333,8 +318,6 @@ __global__ void __launch_bounds__(TcCfg::THREADS, 1)
     }
     ptx::tc_fence_before();
     __syncthreads();
-    // no CTA leaves while a peer may still write into its shared memory or barriers
-    if (CM > 1) ptx::cluster_sync();
     ptx::tc_fence_after();
     if (warp == 1) ptx::tmem_dealloc(tmem, Cfg::TMEM_COLS);
 }
@@ -359,38 +342,15 @@ int get_encoder(EncodeTiledFn* fn) {
     return DBCSR_OK;
 }
 
-// CM = CTAs per cluster along M (1, or 2 with the B tile multicast); tmB's
-// box must then hold TC_TN / CM rows.
-template <int MODE, int CM>
+template <int MODE>
 int launch_mode(const CUtensorMap& tmA, const CUtensorMap& tmB, const OzParams& p, cudaStream_t st, int num_sms) {
     OzParams q = p;
-    q.units = cdiv(p.tiles_m, CM) * p.tiles_n * p.ksegs * p.s;
+    q.units = (int64_t)p.tiles_m * p.tiles_n * p.ksegs * p.s;
     if (q.units <= 0) return DBCSR_OK;
-    const int clusters = (int)std::min<int64_t>(q.units, num_sms / CM);
-    auto kern = k_tc_gemm<MODE, CM>;
+    const int grid = (int)std::min<int64_t>(q.units, num_sms);
+    auto kern = k_tc_gemm<MODE>;
     DB_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg::SMEM));
-    if (CM == 1) {
-        kern<<<clusters, TcCfg::THREADS, TcCfg::SMEM, st>>>(tmA, tmB, q);
-    } else {
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((unsigned)(clusters * CM));
-        cfg.blockDim = dim3(TcCfg::THREADS);
-        cfg.dynamicSmemBytes = TcCfg::SMEM;
-        cfg.stream = st;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = CM;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        // persistent clusters: no more than can be resident at once
-        int active = 0;
-        DB_CUDA(cudaOccupancyMaxActiveClusters(&active, kern, &cfg));
-        if (active < 1) return fail(DBCSR_ERR_CUDA, "tensor-core GEMM: no cluster of 2 CTAs fits on this GPU");
-        if (active < clusters) cfg.gridDim = dim3((unsigned)(active * CM));
-        DB_CUDA(cudaLaunchKernelEx(&cfg, kern, tmA, tmB, q));
-    }
+    kern<<<grid, TcCfg::THREADS, TcCfg::SMEM, st>>>(tmA, tmB, q);
     DB_KCHECK();
     return DBCSR_OK;
 }
@@ -416,21 +376,17 @@ int make_slice_tmap(CUtensorMap* map, const void* base, int64_t ldk, int64_t row
     return DBCSR_OK;
 }
 
-int oz_gemm_launch(const CUtensorMap& tmA, const CUtensorMap& tmB, const OzParams& p, int cluster_m) {
-    if (cluster_m == 2) return launch_mode<MODE_SLICES, 2>(tmA, tmB, p, ctx().stream, ctx().num_sms);
-    return launch_mode<MODE_SLICES, 1>(tmA, tmB, p, ctx().stream, ctx().num_sms);
+int oz_gemm_launch(const CUtensorMap& tmA, const CUtensorMap& tmB, const OzParams& p) {
+    return launch_mode<MODE_SLICES>(tmA, tmB, p, ctx().stream, ctx().num_sms);
 }
 
 int oz_gemm_launch_on(const CUtensorMap& tmA, const CUtensorMap& tmB, const OzParams& p, cudaStream_t st,
                       int num_sms) {
-    return launch_mode<MODE_SLICES, 1>(tmA, tmB, p, st, num_sms);
+    return launch_mode<MODE_SLICES>(tmA, tmB, p, st, num_sms);
 }
 
-int tf32_gemm_launch(const CUtensorMap& tmA, const CUtensorMap& tmB, const OzParams& p, int cluster_m) {
-    if (cluster_m == 2) return launch_mode<MODE_TF32, 2>(tmA, tmB, p, ctx().stream, ctx().num_sms);
-    return launch_mode<MODE_TF32, 1>(tmA, tmB, p, ctx().stream, ctx().num_sms);
+int tf32_gemm_launch(const CUtensorMap& tmA, const CUtensorMap& tmB, const OzParams& p) {
+    return launch_mode<MODE_TF32>(tmA, tmB, p, ctx().stream, ctx().num_sms);
 }
-
-int tc_cluster_m(int64_t M) { return cdiv(M, TC_TM) >= 2 ? 2 : 1; }
 
 }  // namespace dbcsr

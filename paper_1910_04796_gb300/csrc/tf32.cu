@@ -65,8 +65,7 @@ int dgemm_tf32(int64_t M, int64_t N, int64_t K, double alpha, const double* A, i
     CUtensorMap tmA, tmB;
     DB_TRY(make_slice_tmap(&tmA, AT.p, ldk, M, 1, 128, 4));
     const bool wide = N >= 256 && tc256_usable();
-    const int cm = wide ? 1 : tc_cluster_m(M);
-    DB_TRY(make_slice_tmap(&tmB, BT.p, ldk, N, 1, wide ? 256 : 128 / cm, 4));
+    DB_TRY(make_slice_tmap(&tmB, BT.p, ldk, N, 1, wide ? 256 : 128, 4));
     OzParams p{};
     p.M = (int)M;
     p.N = (int)N;
@@ -84,10 +83,11 @@ int dgemm_tf32(int64_t M, int64_t N, int64_t K, double alpha, const double* A, i
     p.alpha = alpha;
     p.beta = beta;
     p.err = ctx().d_flags;
+    p.wait_ns = ctx().wait_ns;
     DB_CUDA(cudaMemsetAsync(p.err, 0, sizeof(int), st));
     timer_kernel_begin();
     if (wide) DB_TRY(tf32_gemm256_launch(tmA, tmB, p));
-    else DB_TRY(tf32_gemm_launch(tmA, tmB, p, cm));
+    else DB_TRY(tf32_gemm_launch(tmA, tmB, p));
     timer_kernel_end();
     int h_err = 0;
     DB_CUDA(cudaMemcpyAsync(&h_err, p.err, sizeof(int), cudaMemcpyDeviceToHost, st));

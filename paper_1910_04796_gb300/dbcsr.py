@@ -71,6 +71,7 @@ SIGNATURES = [
     ("dbcsr_get_stacks", C.c_int, [C.c_char, C.c_char, _P, _P, C.c_int, _IP, C.c_int64, _LP]),
     ("dbcsr_dgemm_emulated_noalloc", C.c_int, [C.c_int64, C.c_int64, C.c_int64, C.c_double, _P, C.c_int64, _P,
                                                C.c_int64, C.c_double, _P, C.c_int64, C.c_int, _P]),
+    ("dbcsr_set_wait_limit", C.c_int, [C.c_int64]),
     ("dbcsr_sync", C.c_int, []),
     ("dbcsr_last_error", C.c_char_p, []),
     ("dbcsr_version", C.c_char_p, []),
@@ -323,6 +324,11 @@ def get_stacks(transa, transb, A: Matrix, B: Matrix, stack_cap=30000) -> np.ndar
 
 def sync():
     _check(load().dbcsr_sync())
+
+
+def set_wait_limit(ns: int = 0):
+    """Limit of each bounded wait in the tensor-core pipelines (dbcsr_set_wait_limit); 0 = default 4 s."""
+    _check(load().dbcsr_set_wait_limit(int(ns)))
 
 
 def version() -> str:

@@ -1,11 +1,20 @@
 """Parity at the workloads' full sizes, in the configuration bench.py times.
 
 The oracle cannot redo whole products of this size, so each test checks
-either sampled C block rows that the oracle computes one by one (same inputs,
-same definition), or, for the largest dense shapes, a property that holds at
-any size: the projection C x = alpha A (B x) + beta C0 x for a random x
-(Freivalds), computed by the oracle's plain loops, within the FP64 rounding
-bound of the two orders of summation.
+sampled rows of C, which the oracle computes one by one from the same inputs
+with the same definition:
+
+* FP64: sampled C block rows (or element rows on the densified path) against
+  the oracle's block product (or its densified GEMM), normwise within 1e-13
+  of the sampled rows' own scale: ||C_rows - C_ref,rows||_F divided by
+  ||op(A)_rows||_F ||op(B)||_F, the bar of the whole product restricted to
+  those rows.
+* Emulated FP64: sampled element rows bit for bit against the oracle's
+  step-by-step emulation. The emulation of a row depends only on that row of
+  op(A) and on all of op(B) (row exponents come from the row itself), so the
+  oracle runs on the sampled rows of op(A) against the whole op(B).
+* Reported precisions (emulated against the near-exact Dot2 product, TF32)
+  within their gates on the same normalisation.
 """
 import numpy as np
 import pytest
@@ -34,6 +43,22 @@ def run(w, path, precision, slices=0):
     return got, st
 
 
+def element_rows(M, rows):
+    """Dense values of the given element rows of a block matrix: (len(rows), total columns)."""
+    rs, cs = np.asarray(M.row_sizes, np.int64), np.asarray(M.col_sizes, np.int64)
+    ro, co = np.concatenate([[0], np.cumsum(rs)]), np.concatenate([[0], np.cumsum(cs)])
+    br, bc = np.asarray(M.blk_row), np.asarray(M.blk_col)
+    offs = np.concatenate([[0], np.cumsum(rs[br] * cs[bc])])
+    out = np.zeros((len(rows), int(co[-1])))
+    for q, r in enumerate(rows):
+        bi = int(np.searchsorted(ro, r, "right") - 1)
+        m = int(rs[bi])
+        for b in np.nonzero(br == bi)[0]:
+            j = int(bc[b])
+            out[q, co[j]:co[j + 1]] = M.data[offs[b] + (r - ro[bi]) + m * np.arange(cs[j])]
+    return out
+
+
 def blocks_of_rows(M, rows):
     """Sub-list (block index + data) of the blocks in the given block rows, CSR order."""
     rs = np.asarray(M.row_sizes, np.int64)
@@ -45,19 +70,19 @@ def blocks_of_rows(M, rows):
     return M.blk_row[keep], M.blk_col[keep], data
 
 
-def frob(M):
-    return float(np.linalg.norm(M.data))
-
-
-def check_rows(got, ref, A, B, tol, exact=False):
+def check_block_rows(got, ref, A, B, tol):
+    """Sampled C block rows of the block product, normwise against the sampled rows of A."""
     rows = np.unique(ref.blk_row)
     gbr, gbc, gdata = blocks_of_rows(got, rows)
     assert np.array_equal(gbr, ref.blk_row) and np.array_equal(gbc, ref.blk_col)
-    if exact:
-        assert np.array_equal(gdata, ref.data)
-    else:
-        err = np.linalg.norm(gdata - ref.data) / (frob(A) * frob(B))
-        assert err <= tol, err
+    _, _, adata = blocks_of_rows(A, rows)
+    err = np.linalg.norm(gdata - ref.data) / (np.linalg.norm(adata) * np.linalg.norm(B.data))
+    assert err <= tol, err
+
+
+def op_dense(M, trans):
+    D = O.densify(M)
+    return np.asfortranarray(D.T) if trans == "T" else D
 
 
 def sample_rows(n, k, seed=0):
@@ -65,47 +90,95 @@ def sample_rows(n, k, seed=0):
     return np.sort(rng.choice(n, size=min(k, n), replace=False)).astype(np.int32)
 
 
+def column_maxima(M):
+    """max |M(l, j)| over each element column j of a block matrix."""
+    rs, cs = np.asarray(M.row_sizes, np.int64), np.asarray(M.col_sizes, np.int64)
+    co = np.concatenate([[0], np.cumsum(cs)])
+    br, bc = np.asarray(M.blk_row), np.asarray(M.blk_col)
+    offs = np.concatenate([[0], np.cumsum(rs[br] * cs[bc])])
+    out = np.zeros(int(co[-1]))
+    for b in range(len(br)):
+        m, n, j = int(rs[br[b]]), int(cs[bc[b]]), int(bc[b])
+        blk = np.abs(M.data[offs[b]:offs[b + 1]].reshape((m, n), order="F")).max(axis=0)
+        out[co[j]:co[j + 1]] = np.maximum(out[co[j]:co[j + 1]], blk)
+    return out
+
+
+def sparse_subproblem(A, B, elem_rows):
+    """The emulation of the sampled rows of A*B (both block-sparse, op = N) as a
+    small dense problem with the same result: the sampled rows of A restricted
+    to the inner indices where they are nonzero, the same rows of B, and one
+    more inner index whose A entries are zero and whose B entries are B's
+    column maxima. Zeros add no slices, row exponents come from the rows
+    themselves, and the appended row gives every column of B its exponent over
+    the whole column."""
+    Arows = element_rows(A, elem_rows)
+    lsel = np.nonzero(np.any(Arows != 0, axis=0))[0]
+    Asub = np.zeros((len(elem_rows), len(lsel) + 1), order="F")
+    Asub[:, :-1] = Arows[:, lsel]
+    Bsub = np.zeros((len(lsel) + 1, int(np.sum(B.col_sizes))), order="F")
+    Bsub[:-1] = element_rows(B, lsel)
+    Bsub[-1] = column_maxima(B)
+    return Asub, Bsub
+
+
+def check_emulated_rows(w, got, elem_rows, s=7):
+    """Sampled element rows equal the oracle's emulation bit for bit."""
+    assert w.transa == "N"
+    full_b = w.B.nblks == len(w.B.row_sizes) * len(w.B.col_sizes)
+    if full_b:
+        Arows = np.asfortranarray(element_rows(w.A, elem_rows))
+        Bd = op_dense(w.B, w.transb)
+    else:
+        assert w.transb == "N"
+        Arows, Bd = sparse_subproblem(w.A, w.B, elem_rows)
+    Cd = np.asfortranarray(element_rows(w.C, elem_rows)) if (w.C is not None and w.beta != 0.0) else \
+        np.zeros((len(elem_rows), Bd.shape[1]), order="F")
+    O.ozaki_gemm(w.alpha, Arows, Bd, w.beta if w.C is not None else 0.0, Cd, s=s)
+    have = element_rows(got, elem_rows)
+    assert np.array_equal(have, Cd), np.abs(have - Cd).max()
+    assert np.count_nonzero(Cd) > 0
+    return Arows, Bd
+
+
 @pytest.mark.parametrize("precision", ["fp64", "ozaki"])
 def test_dense_limit_N11264(precision):
     w = synth.workload_dense_limit()
     got, st = run(w, "auto", precision)
     assert st["path"] == dbcsr.PATH_DENSE
-    rows = sample_rows(512, 3, seed=1)
     if precision == "fp64":
+        rows = sample_rows(512, 3, seed=1)
         ref = O.multiply("N", "N", w.alpha, w.A, w.B, w.beta, w.C, rows=rows)
-        check_rows(got, ref, w.A, w.B, 1e-13)
+        check_block_rows(got, ref, w.A, w.B, 1e-13)
     else:
+        check_emulated_rows(w, got, sample_rows(11264, 6, seed=11))
+        rows = sample_rows(512, 2, seed=1)
         ref = O.multiply("N", "N", w.alpha, w.A, w.B, w.beta, w.C, rows=rows, mode=1)
-        check_rows(got, ref, w.A, w.B, 1e-12)
-
-
-def freivalds(w, got, tol):
-    """||C x - (alpha op(A) (op(B) x) + beta C0 x)|| against FP64 rounding of both sides."""
-    rng = np.random.default_rng(7)
-    Bd = O.densify(w.B)
-    Ad = O.densify(w.A)
-    Bop = Bd.T if w.transb == "T" else Bd
-    Aop = Ad.T if w.transa == "T" else Ad
-    x = np.asfortranarray(rng.uniform(-1, 1, (Bop.shape[1], 1)))
-    bx = np.zeros((Bop.shape[0], 1), order="F")
-    O.dense_gemm("N", "N", 1.0, np.asfortranarray(Bop), x, 0.0, bx)
-    rhs = np.zeros((Aop.shape[0], 1), order="F")
-    O.dense_gemm("N", "N", w.alpha, np.asfortranarray(Aop), bx, 0.0, rhs)
-    Cd = O.densify(got)
-    cx = np.zeros((Cd.shape[0], 1), order="F")
-    O.dense_gemm("N", "N", 1.0, Cd, x, 0.0, cx)
-    # normwise: ||C x - A B x|| / (||A||_F ||B||_F ||x||)
-    err = np.linalg.norm(cx - rhs) / (np.linalg.norm(Ad) * np.linalg.norm(Bd) * np.linalg.norm(x))
-    assert err <= tol, err
+        check_block_rows(got, ref, w.A, w.B, 1e-12)
 
 
 @pytest.mark.parametrize("variant,transb,precision", [("a", "N", "fp64"), ("b", "T", "fp64"),
                                                       ("a", "T", "ozaki"), ("b", "N", "ozaki")])
 def test_tall_skinny_full(variant, transb, precision):
+    # (a) K = 131 072: eight exact-int32 K segments of 16 384 on the emulated path
     w = synth.workload_tall_skinny(variant=variant, transb=transb)
     got, st = run(w, "auto", precision)
     assert st["path"] == dbcsr.PATH_DENSE
-    freivalds(w, got, 1e-13 if precision == "fp64" else 1e-12)
+    M = int(np.sum(w.A.row_sizes))
+    erows = sample_rows(M, 3 if variant == "a" else 6, seed=12)
+    if precision == "ozaki":
+        Arows, Bd = check_emulated_rows(w, got, erows)
+        ref = np.zeros((len(erows), Bd.shape[1]), order="F")
+        O.dense_gemm("N", "N", 1.0, Arows, Bd, 0.0, ref)
+        tol = 1e-12
+    else:
+        Arows = np.asfortranarray(element_rows(w.A, erows))
+        Bd = op_dense(w.B, transb)
+        ref = np.zeros((len(erows), Bd.shape[1]), order="F")
+        O.dense_gemm("N", "N", 1.0, Arows, Bd, 0.0, ref)
+        tol = 1e-13
+    err = np.linalg.norm(element_rows(got, erows) - ref) / (np.linalg.norm(Arows) * np.linalg.norm(Bd))
+    assert err <= tol, err
 
 
 def test_uneven_4000_fp64_stacks():
@@ -114,7 +187,7 @@ def test_uneven_4000_fp64_stacks():
     assert st["path"] == dbcsr.PATH_STACKS
     rows = sample_rows(4000, 24, seed=2)
     ref = O.multiply("N", "N", 1.0, w.A, w.B, 0.0, rows=rows)
-    check_rows(got, ref, w.A, w.B, 1e-13)
+    check_block_rows(got, ref, w.A, w.B, 1e-13)
 
 
 def test_uneven_4000_emulated_stacks():
@@ -122,16 +195,20 @@ def test_uneven_4000_emulated_stacks():
     got, st = run(w, "stacks", "ozaki")
     rows = sample_rows(4000, 24, seed=3)
     ref = O.multiply("N", "N", 1.0, w.A, w.B, 0.0, rows=rows, mode=1)
-    check_rows(got, ref, w.A, w.B, 1e-12)
+    check_block_rows(got, ref, w.A, w.B, 1e-12)
+    M = int(np.sum(w.A.row_sizes))
+    check_emulated_rows(w, got, sample_rows(M, 8, seed=13))
 
 
 @pytest.mark.parametrize("precision,tol", [("ozaki", 1e-12), ("fp64", 1e-13), ("tf32", 1e-2)])
 def test_precision_dense_N16384(precision, tol):
     w = synth.workload_precision_dense()
     got, st = run(w, "dense", precision)
+    if precision == "ozaki":
+        check_emulated_rows(w, got, sample_rows(16384, 4, seed=14))
     rows = sample_rows(512, 2, seed=4)
     ref = O.multiply("N", "N", 1.0, w.A, w.B, 0.0, rows=rows, mode=1)
-    check_rows(got, ref, w.A, w.B, tol)
+    check_block_rows(got, ref, w.A, w.B, tol)
 
 
 def test_precision_sparse_1024_emulated_stacks():
@@ -140,4 +217,5 @@ def test_precision_sparse_1024_emulated_stacks():
     assert st["path"] == dbcsr.PATH_STACKS
     rows = sample_rows(1024, 8, seed=5)
     ref = O.multiply("N", "N", 1.0, w.A, w.B, 0.0, rows=rows, mode=1)
-    check_rows(got, ref, w.A, w.B, 1e-12)
+    check_block_rows(got, ref, w.A, w.B, 1e-12)
+    check_emulated_rows(w, got, sample_rows(32768, 8, seed=15))
