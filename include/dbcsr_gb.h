@@ -106,7 +106,11 @@ typedef struct {
                           Emulated-FP64 stack kernel: 0 = tcgen05 when the mean
                           block edge is at least 12, else mma.sync; 1 = mma.sync
                           (blocks padded to 16); 2 = tcgen05 (blocks padded to
-                          32 x 32, fp32 accumulators in tensor memory)      */
+                          32 x 32, fp32 accumulators in tensor memory).
+                          Emulated-FP64 dense GEMM: 0 = 128 x 256 output
+                          tiles, one CTA each (128 x 128 when N < 256); 4 =
+                          256 x 256 tiles on pairs of CTAs where M and N reach
+                          256 (same results bit for bit)                   */
     int timing;        /* nonzero: time the phases with CUDA events on the
                           library stream (reported by dbcsr_get_stats)        */
     int reuse_plan;    /* nonzero (FP64 stack path): keep this multiply's stack

@@ -928,7 +928,7 @@ int multiply_dense(bool ta, bool tb, double alpha, dbcsr_matrix_s* A, dbcsr_matr
         mark(0);
         if (!c_full) DB_TRY(install_full_index(C, M, N));
         mark(1);
-        DB_TRY(dgemm_ozaki_blocks(A, ta, B, tb, C, alpha, use_old ? beta : 0.0, s, &g_stats.main_flops));
+        DB_TRY(dgemm_ozaki_blocks(A, ta, B, tb, C, alpha, use_old ? beta : 0.0, s, &g_stats.main_flops, o.kernel));
         mark(2);
         mark(3);
         g_stats.c_blocks = C->nblks;

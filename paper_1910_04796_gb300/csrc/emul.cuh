@@ -15,10 +15,11 @@ int dgemm_emulated(int64_t M, int64_t N, int64_t K, double alpha, const double* 
 // slices are cut straight from op(A)'s and op(B)'s blocks, and the result is
 // recombined straight into C's storage, which must already be the fully
 // occupied layout (blocks in CSR order) holding the old values when beta != 0.
-// Only where ozaki_blocks_ok(N) (the 256-wide slice GEMM).
+// Only where ozaki_blocks_ok(N) (the 256-wide slice GEMMs).
 bool ozaki_blocks_ok(int64_t N);
+// kernel: dbcsr_opts.kernel (4 = 256 x 256 tiles on CTA pairs instead of 128 x 256 tiles, one CTA each)
 int dgemm_ozaki_blocks(dbcsr_matrix_s* A, bool ta, dbcsr_matrix_s* B, bool tb, dbcsr_matrix_s* C, double alpha,
-                       double beta, int s, double* main_flops);
+                       double beta, int s, double* main_flops, int kernel);
 
 // TF32 variant of the dense GEMM (tf32.cu).
 int dgemm_tf32(int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda, const double* B,

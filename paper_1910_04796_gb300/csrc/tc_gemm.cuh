@@ -44,4 +44,9 @@ bool tc256_usable();
 int oz_gemm256_launch(const CUtensorMap& tmA, const CUtensorMap& tmB, const OzParams& p);   // writes ws_i32
 int tf32_gemm256_launch(const CUtensorMap& tmA, const CUtensorMap& tmB, const OzParams& p);
 
+// 256 x 256 tiles on CTA pairs (tc_gemm2sm.cu): the same int32 level-sum
+// workspace as the 128 x 256 kernel; tmA's and tmB's boxes hold 128 rows.
+bool tc2sm_usable();
+int oz_gemm2sm_launch(const CUtensorMap& tmA, const CUtensorMap& tmB, const OzParams& p);
+
 }  // namespace dbcsr

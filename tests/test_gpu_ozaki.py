@@ -138,3 +138,35 @@ def test_fused_block_path_uneven_sizes_partial_old_c():
     ref, _, _ = ozaki_ref(A, B, Cm, 1.0, 0.5, 7)
     assert_same_pattern(got, ref)
     assert np.array_equal(got.data, ref.data)
+
+
+# CTA-pair slice GEMM (kernel=4: 256 x 256 tiles, M and N >= 256) against the
+# default one-CTA 128 x 256 kernel and the oracle: ragged M, N, K; several tile rows
+# and columns; two exact-int32 K segments; fully occupied operands take the
+# fused block path, sparse ones the densified one
+@pytest.mark.parametrize("nbr,nbk,nbc,bsr,bsk,bsc", [(13, 9, 25, 22, 22, 22), (30, 40, 20, 22, 22, 22),
+                                                     (17, 1000, 19, 16, 17, 15), (8, 3, 16, 32, 5, 32)])
+def test_pair_tiles_bit_exact(nbr, nbk, nbc, bsr, bsk, bsc):
+    rng = np.random.default_rng(480 + nbk)
+    A = synth.dense_matrix(rng, nbr, nbk, bsr, bsk, dist="wide", scale_exp=2.0)
+    B = synth.dense_matrix(rng, nbk, nbc, bsk, bsc)
+    Cm = synth.dense_matrix(rng, nbr, nbc, bsr, bsc)
+    assert nbr * bsr >= 256 and nbc * bsc >= 256
+    ref, _, _ = ozaki_ref(A, B, Cm, 1.25, -0.5, 7)
+    got, _ = gpu_multiply("N", "N", 1.25, A, B, -0.5, Cm, path="dense", precision="ozaki", kernel=4)
+    one, _ = gpu_multiply("N", "N", 1.25, A, B, -0.5, Cm, path="dense", precision="ozaki")
+    assert_same_pattern(got, ref)
+    assert np.array_equal(got.data, ref.data)
+    assert np.array_equal(one.data, ref.data)
+
+
+@pytest.mark.parametrize("ta,tb", [("T", "N"), ("N", "T"), ("T", "T")])
+def test_pair_tiles_transposes_and_sparse_forced_dense(ta, tb):
+    rng = np.random.default_rng(490)
+    A, B, Cm = synth.random_small(rng, 14, 11, 15, p=0.5, sizes=(13, 22, 32), with_c=True, c_p=0.6)
+    As = synth.transpose_blocks(A) if ta == "T" else A
+    Bs = synth.transpose_blocks(B) if tb == "T" else B
+    got, _ = gpu_multiply(ta, tb, 1.0, As, Bs, 1.0, Cm, path="dense", precision="ozaki", ozaki_slices=6, kernel=4)
+    ref, _, _ = ozaki_ref(A, B, Cm, 1.0, 1.0, 6)
+    assert_same_pattern(got, ref)
+    assert np.array_equal(got.data, ref.data)
