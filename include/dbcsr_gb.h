@@ -149,7 +149,10 @@ typedef struct {
 
 /* Select the stream (a cudaStream_t, may be NULL for the legacy default
  * stream) on which all following work is ordered, and the current CUDA
- * device. Call once before anything else; may be called again to switch. */
+ * device. Call once before anything else; may be called again to switch.
+ * (Sec. III: the GPU execution keeps one library context per thread -- the
+ * paper initialises a cuBLAS context once per thread and draws buffers from
+ * memory pools; here the context is the stream, the device and the pool.) */
 DBCSR_API int dbcsr_init(void *cuda_stream);
 
 /* Route device allocations through the given hooks (NULL, NULL restores the
@@ -178,11 +181,14 @@ DBCSR_API int dbcsr_create(dbcsr_matrix *out, int nblkrows, int nblkcols,
                  int64_t nblks, const int *blk_row, const int *blk_col,
                  const double *data, int data_on_device);
 
-/* Free a matrix and set *m to NULL. NULL or *m == NULL is a no-op. */
+/* Free a matrix and set *m to NULL. NULL or *m == NULL is a no-op. Its device
+ * memory returns to the pool it came from (Sec. III: memory-pool buffers on
+ * the GPU reduce the time spent in allocations). */
 DBCSR_API int dbcsr_release(dbcsr_matrix *m);
 
-/* Block grid, number of stored blocks and of stored elements. Any output
- * pointer may be NULL. */
+/* Block grid, number of stored blocks and of stored elements of a matrix in
+ * the blocked CSR format of Sec. II (block rows and columns of the grid, the
+ * stored blocks of the index). Any output pointer may be NULL. */
 DBCSR_API int dbcsr_get_info(dbcsr_matrix m, int *nblkrows, int *nblkcols, int64_t *nblks,
                    int64_t *nelems);
 
@@ -206,7 +212,9 @@ DBCSR_API int dbcsr_data_ptr(dbcsr_matrix m, double **dev_ptr);
 
 /* Copy block (row, col) to host `out_colmajor` (row_blk_size x col_blk_size
  * doubles, column-major). *found = 1 if the block is stored, else 0 and `out`
- * is left untouched. DBCSR_ERR_ARG for coordinates outside the grid. */
+ * is left untouched. DBCSR_ERR_ARG for coordinates outside the grid.
+ * (Sec. II: a matrix is a set of small dense blocks stored in blocked CSR
+ * form; this reads one of them back, with absent blocks meaning zero.) */
 DBCSR_API int dbcsr_get_block(dbcsr_matrix m, int row, int col, double *out_colmajor, int *found);
 
 /* C = alpha * op(A) * op(B) + beta * C (Sec. II local multiplication; Sec. III

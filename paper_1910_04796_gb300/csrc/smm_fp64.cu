@@ -267,19 +267,21 @@ __global__ void __launch_bounds__(256, Q <= 16 ? 2 : 1) k_smm_fp32(SmmArgs g, co
 }
 
 // FP32 stack kernel for blocks up to 32 x 32: a warp per C block; each
-// product's op(A) and op(B) blocks are staged in the warp's shared memory and
-// lane j accumulates column j of the C block: per inner index l, one
-// conflict-free load of B(l, j) and broadcast 16-byte loads of A(:, l) feed
-// m FMAs. FMA order per element: products in plan order, l ascending.
-// Two staging buffers per warp: the asynchronous copies (cp.async, 4 bytes
-// each) of the next product's blocks run while the current one is computed.
-// Rows m..m+3 of a partial float4 read values that feed accumulators which
-// are never stored.
+// product's op(A) and op(B) blocks are staged in the warp's shared memory
+// (A(i, l) at l * 36 + i, B(l, j) at l * 36 + j: rows 16-byte aligned), and
+// each lane computes an R x CC patch of the C block held in registers: per
+// inner index l it loads R values of A's column l and CC values of B's row l
+// (vector loads) and issues R * CC FMAs. The patch shape follows the block's
+// padded size (8, 16 or 32 per dimension), so that all 32 lanes carry work:
+// 8 x 4 patches for 32 x 32 blocks (32 FMAs per three vector loads), down to
+// 2 x 1 for 8 x 8. FMA order per element: products in plan order, l
+// ascending. Two staging buffers per warp: the asynchronous copies (cp.async,
+// 4 bytes each) of the next product's blocks run while the current one is
+// computed. Patch rows from m and columns from n read whatever the staging
+// buffer holds there and feed accumulators that are never stored.
 constexpr int F32_WARPS = 4;
-constexpr int F32_BSTRIDE = 33;   // sB[j * 33 + l]: lanes j read distinct banks
-constexpr int F32_ASTRIDE = 36;   // sA[l * 36 + i]: 16-byte aligned columns, transposed writes 4-way at most
-
-constexpr int F32_BUF_FLOATS = 32 * F32_ASTRIDE + 32 * F32_BSTRIDE + 32;   // A, B (+ pad to 16 bytes)
+constexpr int F32_STRIDE = 36;   // floats per staged row of A (per l) and of B (per l)
+constexpr int F32_BUF_FLOATS = 2 * 32 * F32_STRIDE;   // A, B
 constexpr int F32_WARP_FLOATS = 2 * F32_BUF_FLOATS;
 constexpr int F32_SMEM = F32_WARPS * F32_WARP_FLOATS * (int)sizeof(float);
 
@@ -297,28 +299,131 @@ __device__ __forceinline__ void f32_stage(const float* ga, const float* gb, int 
     // op(A): element (i, l) of the stored block at i + l*m (TA = 0) or l + i*kk (TA = 1)
     if (!TA) {
         if (lane < m)
-            for (int l = 0; l < kk; l++) cp_async4(a_s + l * F32_ASTRIDE + lane, ga + lane + l * m);
+            for (int l = 0; l < kk; l++) cp_async4(a_s + l * F32_STRIDE + lane, ga + lane + l * m);
     } else {
         if (lane < kk)
-            for (int i = 0; i < m; i++) cp_async4(a_s + lane * F32_ASTRIDE + i, ga + lane + i * kk);
+            for (int i = 0; i < m; i++) cp_async4(a_s + lane * F32_STRIDE + i, ga + lane + i * kk);
     }
     // op(B): element (l, j) at l + j*kk (TB = 0) or j + l*n (TB = 1)
     if (!TB) {
         if (lane < kk)
-            for (int j = 0; j < n; j++) cp_async4(b_s + j * F32_BSTRIDE + lane, gb + lane + j * kk);
+            for (int j = 0; j < n; j++) cp_async4(b_s + lane * F32_STRIDE + j, gb + lane + j * kk);
     } else {
         if (lane < n)
-            for (int l = 0; l < kk; l++) cp_async4(b_s + lane * F32_BSTRIDE + l, gb + lane + l * n);
+            for (int l = 0; l < kk; l++) cp_async4(b_s + l * F32_STRIDE + lane, gb + lane + l * n);
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
+// X consecutive floats from 16- (X = 4) or 8-byte (X = 2) aligned shared memory
+template <int X>
+__device__ __forceinline__ void f32_load(const float* p, float (&v)[X]) {
+    if (X == 4) {
+        const float4 t = *reinterpret_cast<const float4*>(p);
+        v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+    } else if (X == 2) {
+        const float2 t = *reinterpret_cast<const float2*>(p);
+        v[0] = t.x; v[1] = t.y;
+    } else {
+#pragma unroll
+        for (int x = 0; x < X; x++) v[x] = p[x];
+    }
+}
+// one C block (m x n, both at most 32) on one warp with R x CC patches, LC
+// lanes across the columns and 32 / LC down the rows
+template <int TA, int TB, int R, int CC, int LC>
+__device__ __forceinline__ void f32_cblock(const SmmArgs& g, int64_t cb, int m, int n, float* wbuf, int lane,
+                                           const BlasUpd& bu) {
+    const int row0 = (lane / LC) * R, col0 = (lane % LC) * CC;
+    const int64_t p0 = g.c_pstart[cb], p1 = g.c_pstart[cb + 1];
+    float acc[R][CC];
+#pragma unroll
+    for (int r = 0; r < R; r++)
+#pragma unroll
+        for (int c = 0; c < CC; c++) acc[r][c] = 0.f;
+    // operands of product p: offsets and inner size
+    auto operands = [&](int64_t p, const float*& ga, const float*& gb, int& kk) {
+        const int2 pr = g.prod[p];
+        const int64_t ao = g.A.off[pr.x], bo = g.B.off[pr.y];
+        kk = (int)(g.A.off[pr.x + 1] - ao) / m;
+        ga = g.A32 + ao;
+        gb = g.B32 + bo;
+    };
+    const float *ga = nullptr, *gb = nullptr;
+    int kk = 0;
+    if (p0 < p1) {
+        operands(p0, ga, gb, kk);
+        f32_stage<TA, TB>(ga, gb, m, n, kk, wbuf, wbuf + 32 * F32_STRIDE, lane);
+    }
+    for (int64_t p = p0; p < p1; p++) {
+        const int cur_kk = kk;
+        const float* a_s = wbuf + ((p - p0) & 1) * F32_BUF_FLOATS;
+        const float* b_s = a_s + 32 * F32_STRIDE;
+        if (p + 1 < p1) {
+            // the other buffer was last read by product p - 1, finished by every lane
+            __syncwarp();
+            operands(p + 1, ga, gb, kk);
+            float* na = wbuf + ((p + 1 - p0) & 1) * F32_BUF_FLOATS;
+            f32_stage<TA, TB>(ga, gb, m, n, kk, na, na + 32 * F32_STRIDE, lane);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        __syncwarp();   // product p's blocks are in shared memory for every lane
+        const float* ar = a_s + row0;
+        const float* bc = b_s + col0;
+#pragma unroll 2
+        for (int l = 0; l < cur_kk; l++) {
+            float av[R], bv[CC];
+            f32_load<R>(ar + l * F32_STRIDE, av);
+            f32_load<CC>(bc + l * F32_STRIDE, bv);
+#pragma unroll
+            for (int r = 0; r < R; r++)
+#pragma unroll
+                for (int c = 0; c < CC; c++) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
+        }
+    }
+    __syncwarp();   // the next C block's first copies overwrite buffer 0
+    // alpha / beta in FP64, column-major C block
+    double* cout = g.Cd + g.c_off[cb];
+    const int o = g.c_old ? g.c_old[cb] : -1;
+    const double* cold = o >= 0 ? g.Cold + g.Cold_off[o] : nullptr;
+#pragma unroll
+    for (int c = 0; c < CC; c++) {
+        const int j = col0 + c;
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const int i = row0 + r;
+            if (i < m && j < n) {
+                const int64_t e = (int64_t)j * m + i;
+                cout[e] = cold ? bu.update((double)acc[r][c], cold[e]) : bu.scale((double)acc[r][c]);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ int f32_class(int x) { return x <= 8 ? 0 : (x <= 16 ? 1 : 2); }
+
+// patch class of each C block (rows 8 / 16 / 32 x columns 8 / 16 / 32), for
+// a stable sort that lets the warps of an SM run one code path at a time
+// (interleaved classes thrash the instruction cache)
+__global__ void k_f32_classify(int64_t nC, const int* __restrict__ c_row, const int* __restrict__ c_col,
+                               const int* __restrict__ rsC, const int* __restrict__ csC, uint32_t* __restrict__ key,
+                               uint32_t* __restrict__ idx) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= nC) return;
+    const int m = rsC[c_row[q]], n = csC[c_col[q]];
+    key[q] = (uint32_t)((m <= 8 ? 0 : (m <= 16 ? 1 : 2)) * 3 + (n <= 8 ? 0 : (n <= 16 ? 1 : 2)));
+    idx[q] = (uint32_t)q;
+}
+
 template <int TA, int TB>
-__global__ void __launch_bounds__(32 * F32_WARPS) k_smm_f32_tile(SmmArgs g, int chunk) {
+__global__ void __launch_bounds__(32 * F32_WARPS) k_smm_f32_tile(SmmArgs g, const uint32_t* __restrict__ order,
+                                                                 int chunk) {
     extern __shared__ __align__(16) float f32_smem[];
     __shared__ int s_cb[F32_WARPS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float* wbuf = f32_smem + warp * F32_WARP_FLOATS;   // per buffer: A(i, l) at l * 36 + i, then B(l, j) at j * 33 + l
+    float* wbuf = f32_smem + warp * F32_WARP_FLOATS;
     const BlasUpd bu(g.alpha, g.beta);
     for (;;) {
         if (lane == 0) s_cb[warp] = (int)atomicAdd(g.counter, (unsigned long long)chunk);
@@ -327,70 +432,20 @@ __global__ void __launch_bounds__(32 * F32_WARPS) k_smm_f32_tile(SmmArgs g, int 
         __syncwarp();
         if (base >= g.nC) break;
         const int64_t cend = min(base + (int64_t)chunk, g.nC);
-        for (int64_t cb = base; cb < cend; cb++) {
+        for (int64_t q = base; q < cend; q++) {
+            const int64_t cb = order ? (int64_t)order[q] : q;
             const int m = g.rsC[g.c_row[cb]], n = g.csC[g.c_col[cb]];
-            const int64_t p0 = g.c_pstart[cb], p1 = g.c_pstart[cb + 1];
-            float acc[32];
-#pragma unroll
-            for (int i = 0; i < 32; i++) acc[i] = 0.f;
-            // operands of product p: offsets and inner size
-            auto operands = [&](int64_t p, const float*& ga, const float*& gb, int& kk) {
-                const int2 pr = g.prod[p];
-                const int64_t ao = g.A.off[pr.x], bo = g.B.off[pr.y];
-                kk = (int)(g.A.off[pr.x + 1] - ao) / m;
-                ga = g.A32 + ao;
-                gb = g.B32 + bo;
-            };
-            const float *ga = nullptr, *gb = nullptr;
-            int kk = 0;
-            if (p0 < p1) {
-                operands(p0, ga, gb, kk);
-                f32_stage<TA, TB>(ga, gb, m, n, kk, wbuf, wbuf + 32 * F32_ASTRIDE, lane);
-            }
-            for (int64_t p = p0; p < p1; p++) {
-                const int cur_kk = kk;
-                float* a_s = wbuf + ((p - p0) & 1) * F32_BUF_FLOATS;
-                float* b_s = a_s + 32 * F32_ASTRIDE;
-                if (p + 1 < p1) {
-                    // the other buffer was last read by product p - 1, finished by every lane
-                    __syncwarp();
-                    operands(p + 1, ga, gb, kk);
-                    float* na = wbuf + ((p + 1 - p0) & 1) * F32_BUF_FLOATS;
-                    f32_stage<TA, TB>(ga, gb, m, n, kk, na, na + 32 * F32_ASTRIDE, lane);
-                    asm volatile("cp.async.wait_group 1;" ::: "memory");
-                } else {
-                    asm volatile("cp.async.wait_group 0;" ::: "memory");
-                }
-                __syncwarp();   // product p's blocks are in shared memory for every lane
-                if (lane < n) {
-                    for (int l = 0; l < cur_kk; l++) {
-                        const float b = b_s[lane * F32_BSTRIDE + l];
-                        const float4* ac = reinterpret_cast<const float4*>(a_s + l * F32_ASTRIDE);
-#pragma unroll
-                        for (int i4 = 0; i4 < 8; i4++) {
-                            if (4 * i4 < m) {
-                                const float4 av = ac[i4];
-                                acc[4 * i4 + 0] = fmaf(av.x, b, acc[4 * i4 + 0]);
-                                acc[4 * i4 + 1] = fmaf(av.y, b, acc[4 * i4 + 1]);
-                                acc[4 * i4 + 2] = fmaf(av.z, b, acc[4 * i4 + 2]);
-                                acc[4 * i4 + 3] = fmaf(av.w, b, acc[4 * i4 + 3]);
-                            }
-                        }
-                    }
-                }
-            }
-            __syncwarp();   // the next C block's first copies overwrite buffer 0
-            // column j = lane of the C block; alpha / beta in FP64
-            if (lane < n) {
-                double* cout = g.Cd + g.c_off[cb] + (int64_t)lane * m;
-                const int o = g.c_old ? g.c_old[cb] : -1;
-                const double* cold = o >= 0 ? g.Cold + g.Cold_off[o] + (int64_t)lane * m : nullptr;
-#pragma unroll
-                for (int i = 0; i < 32; i++) {
-                    if (i < m) {
-                        cout[i] = cold ? bu.update((double)acc[i], cold[i]) : bu.scale((double)acc[i]);
-                    }
-                }
+            // patch shape by padded size (rows 8 / 16 / 32) x (columns 8 / 16 / 32)
+            switch (f32_class(m) * 3 + f32_class(n)) {
+                case 0: f32_cblock<TA, TB, 2, 1, 8>(g, cb, m, n, wbuf, lane, bu); break;   //  8 x  8
+                case 1: f32_cblock<TA, TB, 2, 2, 8>(g, cb, m, n, wbuf, lane, bu); break;   //  8 x 16
+                case 2: f32_cblock<TA, TB, 2, 4, 8>(g, cb, m, n, wbuf, lane, bu); break;   //  8 x 32
+                case 3: f32_cblock<TA, TB, 2, 2, 4>(g, cb, m, n, wbuf, lane, bu); break;   // 16 x  8
+                case 4: f32_cblock<TA, TB, 4, 2, 8>(g, cb, m, n, wbuf, lane, bu); break;   // 16 x 16
+                case 5: f32_cblock<TA, TB, 4, 4, 8>(g, cb, m, n, wbuf, lane, bu); break;   // 16 x 32
+                case 6: f32_cblock<TA, TB, 4, 2, 4>(g, cb, m, n, wbuf, lane, bu); break;   // 32 x  8
+                case 7: f32_cblock<TA, TB, 4, 4, 4>(g, cb, m, n, wbuf, lane, bu); break;   // 32 x 16
+                default: f32_cblock<TA, TB, 8, 4, 8>(g, cb, m, n, wbuf, lane, bu); break;  // 32 x 32
             }
         }
     }
@@ -574,6 +629,14 @@ int smm_fp32_dispatch(const SmmArgs& g, int max_mn, int max_edge) {
     if (g.nC == 0) return DBCSR_OK;
     if (max_edge <= 32) {
         cudaStream_t st = ctx().stream;
+        if (g.nC >= (int64_t)UINT32_MAX) return fail(DBCSR_ERR_OVERFLOW, "stack kernels: too many C blocks");
+        DBuf<uint32_t> key, order;
+        DB_TRY(key.alloc(g.nC));
+        DB_TRY(order.alloc(g.nC));
+        k_f32_classify<<<(unsigned)cdiv(g.nC, 256), 256, 0, st>>>(g.nC, g.c_row, g.c_col, g.rsC, g.csC, key.p,
+                                                                  order.p);
+        DB_KCHECK();
+        DB_TRY(radix_sort_u32(key.p, order.p, g.nC, 4));
         int grid = ctx().num_sms * 3;
         if ((int64_t)grid * F32_WARPS > g.nC) grid = (int)cdiv(g.nC, F32_WARPS);
         const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(16, g.nC / ((int64_t)grid * F32_WARPS * 4)));
@@ -582,7 +645,7 @@ int smm_fp32_dispatch(const SmmArgs& g, int max_mn, int max_edge) {
     do {                                                                                                \
         DB_CUDA(cudaFuncSetAttribute(k_smm_f32_tile<TA_, TB_>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                      F32_SMEM));                                                        \
-        k_smm_f32_tile<TA_, TB_><<<grid, 32 * F32_WARPS, F32_SMEM, st>>>(g, chunk);                     \
+        k_smm_f32_tile<TA_, TB_><<<grid, 32 * F32_WARPS, F32_SMEM, st>>>(g, order.p, chunk);            \
     } while (0)
         if (!ta && !tb) DB_LAUNCH_F32(0, 0);
         else if (ta && !tb) DB_LAUNCH_F32(1, 0);
