@@ -70,10 +70,12 @@ typedef void (*dbcsr_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
 
 /* Execution path of dbcsr_multiply (Sec. II stacks vs Sec. III densification). */
 #define DBCSR_PATH_AUTO   0  /* dense path when op(A) and op(B) are 100% occupied (FP32:
-                                always stacks); else stacks, except where the stack kernels
-                                do not apply: emulated FP64 with a block edge above 32 and
-                                TF32 take the dense path (Sec. II: blocks beyond the small
-                                kernels' range go to a GEMM) */
+                                always stacks; FP64 with every block edge up to 32: stacks,
+                                measured faster there than the FP64 dense GEMM); else
+                                stacks, except where the stack kernels do not apply:
+                                emulated FP64 with a block edge above 32 and TF32 take the
+                                dense path (Sec. II: blocks beyond the small kernels' range
+                                go to a GEMM) */
 #define DBCSR_PATH_STACKS 1  /* stacks of block products, batched small-GEMM kernels. FP64
                                 and FP32: any block size. Emulated FP64: block edges up
                                 to 32 (DBCSR_ERR_ARG above). TF32: none (DBCSR_ERR_ARG) */
@@ -95,8 +97,9 @@ typedef struct {
     int path;          /* DBCSR_PATH_*                                        */
     int precision;     /* DBCSR_PREC_*                                        */
     int ozaki_slices;  /* slices per operand for DBCSR_PREC_OZAKI; 0 = default (7) */
-    int kernel;        /* FP64 stack kernel: 0 = per-shape table set with
-                          dbcsr_set_tuning (variant 0 for untuned shapes);
+    int kernel;        /* FP64 stack kernel: 0 = per-shape tables set with
+                          dbcsr_set_tuning_mnk and dbcsr_set_tuning (variant
+                          0 for untuned shapes);
                           v = 1..4 forces variant v-1 for every block:
                           0: one warp per C block;
                           1: the same as 0 (kept for tables that name it);
@@ -241,6 +244,17 @@ DBCSR_API int dbcsr_get_stats(dbcsr_stats *out);
  * m[q] x n[q] (1..128) use variant[q] (0..3, see dbcsr_opts.kernel).
  * Replaces the previous table; count = 0 clears it. Host arrays. */
 DBCSR_API int dbcsr_set_tuning(const int *m, const int *n, const int *variant, int count);
+
+/* Per-(m, n, k) choice of the FP64 stack kernel, over the (m, n) table of
+ * dbcsr_set_tuning (Sec. II: LIBCUSMM's kernels are tuned per block shape
+ * m, n, k). count entries: a C block of size m[q] x n[q] whose first product
+ * has inner size k[q] (all 1..32) uses variant[q] (0..3). C blocks of shapes
+ * without an entry fall back to the (m, n) table. Replaces the previous
+ * (m, n, k) table; count = 0 clears it. Host arrays; DBCSR_ERR_ARG for NULL
+ * arrays with count > 0 or an entry out of range (the table is then left as
+ * it was). The tables reach the GPU once per change, before the next
+ * multiply that reads them. */
+DBCSR_API int dbcsr_set_tuning_mnk(const int *m, const int *n, const int *k, const int *variant, int count);
 
 /* The stack list of Sec. II (Traversal + Generation), as the GPU builds it
  * for op(A) * op(B): one entry per block product, 7 int32 each:

@@ -180,6 +180,11 @@ int setup_sizes(dbcsr_matrix_s* m, int nbr, int nbc, const int* rs, const int* c
     for (int j = 0; j < nbc; j++) m->h_coff[j + 1] = m->h_coff[j] + cs[j];
     m->max_rs = nbr ? *std::max_element(rs, rs + nbr) : 0;
     m->max_cs = nbc ? *std::max_element(cs, cs + nbc) : 0;
+    for (auto* u : {&m->u_rs, &m->u_cs}) {
+        *u = (u == &m->u_rs) ? m->h_rs : m->h_cs;
+        std::sort(u->begin(), u->end());
+        u->erase(std::unique(u->begin(), u->end()), u->end());
+    }
     DB_TRY(dalloc(&m->d_rs, (size_t)nbr + 1));
     DB_TRY(dalloc(&m->d_cs, (size_t)nbc + 1));
     DB_TRY(dalloc(&m->d_roff, (size_t)nbr + 1));
@@ -464,6 +469,12 @@ int dbcsr_set_tuning(const int* m, const int* n, const int* variant, int count) 
     return smm_set_table(m, n, variant, count);
 }
 
+int dbcsr_set_tuning_mnk(const int* m, const int* n, const int* k, const int* variant, int count) {
+    if (count < 0 || (count > 0 && (!m || !n || !k || !variant)))
+        return fail(DBCSR_ERR_ARG, "set_tuning_mnk: bad arguments");
+    return smm_set_table_mnk(m, n, k, variant, count);
+}
+
 int dbcsr_get_stats(dbcsr_stats* out) {
     if (!out) return fail(DBCSR_ERR_ARG, "get_stats: NULL");
     *out = g_stats;
@@ -571,7 +582,8 @@ bool plan_matches(const ReusePlan* rp, bool ta, bool tb, double alpha, double be
 
 // The FP64 product kernels over C blocks [b0, b1) of the plan (one contiguous
 // run of C block rows): the same arguments with the C-block arrays offset.
-int fp64_stack_run(const SmmArgs& g0, int64_t b0, int64_t b1, dbcsr_matrix_s* C, const dbcsr_opts& o) {
+int fp64_stack_run(const SmmArgs& g0, int64_t b0, int64_t b1, dbcsr_matrix_s* C, const dbcsr_opts& o,
+                   int team_bound) {
     if (b1 <= b0) return DBCSR_OK;
     SmmArgs g = g0;
     g.nC = b1 - b0;
@@ -581,7 +593,7 @@ int fp64_stack_run(const SmmArgs& g0, int64_t b0, int64_t b1, dbcsr_matrix_s* C,
     if (g.c_old) g.c_old += b0;
     g.c_pstart += b0;
     DB_CUDA(cudaMemsetAsync(g.counter, 0, sizeof(unsigned long long), g_ctx.stream));
-    return smm_fp64_dispatch(g, C->max_rs * C->max_cs, o.kernel);
+    return smm_fp64_dispatch(g, C->max_rs * C->max_cs, o.kernel, team_bound);
 }
 
 // Hybrid partial densification: Sec. III coalesces all blocks of a dense
@@ -653,7 +665,7 @@ int hybrid_products(const SmmArgs& g, const StackPlan& P, double* data, bool ta,
         const int64_t b0 = crp[r0], b1 = crp[r1];
         if (!dense_run[q]) {
             if (o.precision == DBCSR_PREC_FP64) {
-                DB_TRY(fp64_stack_run(g, b0, b1, C, o));
+                DB_TRY(fp64_stack_run(g, b0, b1, C, o, smm_table_team_bound(C->u_rs, C->u_cs, ta ? A->u_rs : A->u_cs)));
             } else {
                 sparse.push_back({b0, b1});   // emulated: one call, operands sliced once
                 sparse_prod += ps[b1] - ps[b0];
@@ -779,7 +791,8 @@ int multiply_stacks(bool ta, bool tb, double alpha, dbcsr_matrix_s* A, dbcsr_mat
         rc = hybrid_products(g, P, data, ta, tb, alpha, A, B, beta, use_old, C, o);
     } else if (o.precision == DBCSR_PREC_FP64) {
         timer_kernel_begin();
-        rc = smm_fp64_dispatch(g, C->max_rs * C->max_cs, o.kernel);
+        rc = smm_fp64_dispatch(g, C->max_rs * C->max_cs, o.kernel,
+                               smm_table_team_bound(C->u_rs, C->u_cs, ta ? A->u_rs : A->u_cs));
         timer_kernel_end();
         g_stats.main_flops = g_stats.useful_flops;
     } else if (o.precision == DBCSR_PREC_FP32) {
@@ -1020,7 +1033,10 @@ extern "C" int dbcsr_multiply(char transa, char transb, double alpha, dbcsr_matr
         const bool b_full = B->nblks == (int64_t)B->nbr * B->nbc && B->nblks > 0;
         const int max_edge = std::max(std::max(A->max_rs, A->max_cs), std::max(B->max_rs, B->max_cs));
         if (o.precision == DBCSR_PREC_FP32) path = DBCSR_PATH_STACKS;
-        else if (a_full && b_full) path = DBCSR_PATH_DENSE;
+        else if (a_full && b_full)
+            // FP64 blocks up to 32 x 32 run faster on the stack kernels than
+            // densified on the FP64 tensor-core GEMM, whatever the occupancy
+            path = (o.precision == DBCSR_PREC_FP64 && max_edge <= 32) ? DBCSR_PATH_STACKS : DBCSR_PATH_DENSE;
         else if (o.precision == DBCSR_PREC_TF32) path = DBCSR_PATH_DENSE;
         else if (o.precision == DBCSR_PREC_OZAKI && max_edge > EMUL_STACK_MAX_EDGE) path = DBCSR_PATH_DENSE;
         else path = DBCSR_PATH_STACKS;

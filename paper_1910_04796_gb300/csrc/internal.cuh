@@ -115,6 +115,7 @@ struct dbcsr_matrix_s {
     int nbr = 0, nbc = 0;
     int64_t nblks = 0, nelems = 0;
     std::vector<int> h_rs, h_cs;
+    std::vector<int> u_rs, u_cs;   // distinct block sizes, ascending
     std::vector<int64_t> h_roff, h_coff;
     int max_rs = 0, max_cs = 0;
     int* d_rs = nullptr;

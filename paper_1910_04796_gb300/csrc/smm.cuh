@@ -37,10 +37,18 @@ constexpr int SMM_NUM_VARIANTS = 4;
 
 // variant 0 over every C block
 int smm_fp64_generic(const SmmArgs& g, int max_mn);
-// kernel = 0: per-(m,n) table (variant 0 where untuned); kernel = v >= 1: variant v-1
-int smm_fp64_dispatch(const SmmArgs& g, int max_mn, int kernel);
+// kernel = 0: the tuning tables (variant 0 where untuned); kernel = v >= 1:
+// variant v-1. team_bound: the largest team index (0: one warp, 1: two, 2:
+// four) the tables can give these C blocks (smm_table_team_bound); with 0 the
+// table path launches the one-warp kernel directly.
+int smm_fp64_dispatch(const SmmArgs& g, int max_mn, int kernel, int team_bound = 2);
+// Largest team index the tuning tables give a C block of m in ms, n in ns whose
+// products have inner sizes in ks (host check, conservative: 2 when unsure)
+int smm_table_team_bound(const std::vector<int>& ms, const std::vector<int>& ns, const std::vector<int>& ks);
 // (m, n) -> variant entries of the tuning table (replaces the table)
 int smm_set_table(const int* m, const int* n, const int* variant, int count);
+// (m, n, k) -> variant entries, m, n, k in 1..32 (replaces that table; count 0 clears it)
+int smm_set_table_mnk(const int* m, const int* n, const int* k, const int* variant, int count);
 
 // FP32 stack kernels over every C block (g.A32, g.B32 set), one warp per C
 // block; max_edge: the largest block edge of op(A) and op(B)

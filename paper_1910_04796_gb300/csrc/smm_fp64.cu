@@ -235,13 +235,13 @@ struct SmmGroups {
     const int* counts;            // C blocks per team size 1, 2, 4 (nullptr: see n_all)
     int64_t n_all;
     unsigned long long* ctr;      // one zeroed counter per group
+    int64_t stride;               // group k's C blocks at list + k * stride
 };
 
 template <int Q, int TA, int TB>
 __global__ void __launch_bounds__(256, Q <= 16 ? 2 : 1)
     k_smm_fp64_all(SmmArgs g, const uint32_t* __restrict__ list, SmmGroups gr) {
     extern __shared__ double s_red[];                 // [teams][W-1][Q][32] partial sums, W <= 4
-    int64_t start = 0;
 #pragma unroll 1
     for (int k = 0; k < 3; k++) {
         const int64_t cnt = gr.counts ? (int64_t)gr.counts[k] : (k == 0 ? gr.n_all : 0);
@@ -249,13 +249,12 @@ __global__ void __launch_bounds__(256, Q <= 16 ? 2 : 1)
             const int64_t teams = (int64_t)gridDim.x * (8 >> k);
             // C blocks per grab: up to 32, at least ~8 grabs per team
             const int chunk = (int)max((int64_t)1, min((int64_t)32, cnt / (teams * 8)));
-            const uint32_t* l = list ? list + start : nullptr;
+            const uint32_t* l = list ? list + k * gr.stride : nullptr;
             if (k == 0) smm_body<double, Q, TA, TB, 1>(g, g.A.data, g.B.data, l, cnt, chunk, s_red, gr.ctr);
             else if (k == 1) smm_body<double, Q, TA, TB, 2>(g, g.A.data, g.B.data, l, cnt, chunk, s_red, gr.ctr + 1);
             else smm_body<double, Q, TA, TB, 4>(g, g.A.data, g.B.data, l, cnt, chunk, s_red, gr.ctr + 2);
             __syncthreads();   // every team done with this group's barriers and partial sums
         }
-        start += cnt;
     }
 }
 
@@ -484,36 +483,65 @@ int launch_fp32(const SmmArgs& g, int qidx, const uint32_t* list, int64_t nlist)
     }
 }
 
-// team-size index of every C block (0: one warp, 1: two, 2: four), from the
-// tuning table or a forced variant; counts aggregated per CTA before the
-// global atomics
-__global__ void k_classify_team(int64_t nC, const int* __restrict__ c_row, const int* __restrict__ c_col,
-                                const int64_t* __restrict__ c_pstart, const int* __restrict__ rsC,
-                                const int* __restrict__ csC, const signed char* __restrict__ table, int tdim,
-                                int forced, uint32_t* __restrict__ key, uint32_t* __restrict__ idx,
+// Team size of each C block (index 0: one warp, 1: two, 2: four): forced,
+// else from the tuning tables -- the (m, n, k) entry when one is set for the
+// block's shape and the inner size k of its first product (tab3, kdim^3
+// entries, m, n, k < kdim), else the (m, n) entry (table, tdim^2 entries),
+// else one warp -- and the C blocks partitioned by it: group t at lists + t*nC,
+// filled in CTA-sized runs (one reservation per CTA and group, ascending order
+// inside a run). counts[t] must be zero on entry. Every C block is computed by
+// one team with its products in plan order, so the order inside a group
+// changes no result.
+__global__ void __launch_bounds__(256) k_classify_team(int64_t nC, const int* __restrict__ c_row,
+                                const int* __restrict__ c_col, const int64_t* __restrict__ c_pstart,
+                                const int* __restrict__ rsC, const int* __restrict__ csC,
+                                const signed char* __restrict__ table, int tdim,
+                                const signed char* __restrict__ tab3, int kdim, const int2* __restrict__ prod,
+                                const int64_t* __restrict__ a_off, int forced, uint32_t* __restrict__ lists,
                                 int* __restrict__ counts) {
-    __shared__ int sc[3];
-    if (threadIdx.x < 3) sc[threadIdx.x] = 0;
-    __syncthreads();
+    __shared__ int s_wcnt[8][3];   // blocks per warp and group
+    __shared__ int s_base[3];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int t = -1;
     if (b < nC) {
         const int m = rsC[c_row[b]], n = csC[c_col[b]];
         int v = forced >= 0 ? forced : 0;
-        if (forced < 0 && table && m < tdim && n < tdim) {
-            const int t = table[m * tdim + n];
-            if (t >= 0) v = t;
+        if (forced < 0 && m < tdim && n < tdim) {
+            int tv = table ? table[m * tdim + n] : -1;
+            if (tab3 && m < kdim && n < kdim && c_pstart[b + 1] > c_pstart[b]) {
+                const int ax = prod[c_pstart[b]].x;
+                const int k = (int)((a_off[ax + 1] - a_off[ax]) / m);
+                if (k < kdim && tab3[(m * kdim + n) * kdim + k] >= 0) tv = tab3[(m * kdim + n) * kdim + k];
+            }
+            if (tv >= 0) v = tv;
             // a team only pays off with at least two products per warp; a C block
             // with fewer runs on one warp (its team-mates would wait at the barrier)
             const int64_t nprod = c_pstart[b + 1] - c_pstart[b];
             if (nprod < 2 * ((v == 2) ? 2 : (v == 3) ? 4 : 1)) v = 0;   // kTeamWarps[v]
         }
-        const int t = (v == 2) ? 1 : (v == 3) ? 2 : 0;                   // team size 1, 2, 4
-        key[b] = (uint32_t)t;
-        idx[b] = (uint32_t)b;
-        atomicAdd(&sc[t], 1);
+        t = (v == 2) ? 1 : (v == 3) ? 2 : 0;
+    }
+    int rank[3];
+#pragma unroll
+    for (int q = 0; q < 3; q++) {
+        const unsigned msk = __ballot_sync(0xffffffffu, t == q);
+        rank[q] = __popc(msk & ((1u << lane) - 1u));
+        if (lane == 0) s_wcnt[warp][q] = __popc(msk);
     }
     __syncthreads();
-    if (threadIdx.x < 3 && sc[threadIdx.x]) atomicAdd(&counts[threadIdx.x], sc[threadIdx.x]);
+    if (threadIdx.x < 3) {
+        const int q = threadIdx.x;
+        int tot = 0;
+        for (int w = 0; w < 8; w++) {
+            const int c = s_wcnt[w][q];
+            s_wcnt[w][q] = tot;   // exclusive prefix over the CTA's warps
+            tot += c;
+        }
+        s_base[q] = tot ? atomicAdd(&counts[q], tot) : 0;
+    }
+    __syncthreads();
+    if (t >= 0) lists[t * nC + s_base[t] + s_wcnt[warp][t] + rank[t]] = (uint32_t)b;
 }
 
 template <int Q>
@@ -555,12 +583,60 @@ int launch_all(const SmmArgs& g, int max_mn, const uint32_t* list, const SmmGrou
     }
 }
 
-// (m, n) -> variant table set by dbcsr_set_tuning; -1 = default
+// (m, n) -> variant table set by dbcsr_set_tuning, and (m, n, k) -> variant
+// set by dbcsr_set_tuning_mnk; -1 = not set. The device copy is kept for the
+// process and uploaded again before the first multiply after a change; the
+// upload first waits for the last launch that read it (an event), which may sit
+// on another stream after dbcsr_init switched streams.
 constexpr int TDIM = 129;
-std::vector<signed char> g_table(TDIM* TDIM, -1);
+constexpr int KDIM = 33;
+constexpr size_t TABLE_BYTES = TDIM * TDIM + KDIM * KDIM * KDIM;
+std::vector<signed char> g_table(TABLE_BYTES, -1);
 bool g_table_used = false;
+bool g_tab3_used = false;
+bool g_table_dirty = true;
+signed char* g_dtable = nullptr;
+cudaEvent_t g_table_ev = nullptr;
+bool g_table_ev_pending = false;
+
+inline int team_of(int v) { return (v == 2) ? 1 : (v == 3) ? 2 : 0; }
+
+int device_table(const signed char** out) {
+    cudaStream_t st = ctx().stream;
+    if (!g_dtable) {
+        cudaError_t e = cudaMalloc(&g_dtable, TABLE_BYTES);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            g_dtable = nullptr;
+            return fail(DBCSR_ERR_ALLOC, std::string("tuning table: ") + cudaGetErrorString(e));
+        }
+        DB_CUDA(cudaEventCreateWithFlags(&g_table_ev, cudaEventDisableTiming));
+        g_table_dirty = true;
+    }
+    if (g_table_dirty) {
+        if (g_table_ev_pending) DB_CUDA(cudaEventSynchronize(g_table_ev));
+        DB_CUDA(cudaMemcpyAsync(g_dtable, g_table.data(), TABLE_BYTES, cudaMemcpyHostToDevice, st));
+        g_table_dirty = false;
+    }
+    *out = g_dtable;
+    return DBCSR_OK;
+}
 
 }  // namespace
+
+int smm_set_table_mnk(const int* m, const int* n, const int* k, const int* variant, int count) {
+    std::vector<signed char> t(KDIM * KDIM * KDIM, -1);
+    for (int q = 0; q < count; q++) {
+        if (m[q] < 1 || m[q] >= KDIM || n[q] < 1 || n[q] >= KDIM || k[q] < 1 || k[q] >= KDIM || variant[q] < 0 ||
+            variant[q] >= SMM_NUM_VARIANTS)
+            return fail(DBCSR_ERR_ARG, "set_tuning_mnk: entry " + std::to_string(q) + " out of range");
+        t[(m[q] * KDIM + n[q]) * KDIM + k[q]] = (signed char)variant[q];
+    }
+    std::copy(t.begin(), t.end(), g_table.begin() + TDIM * TDIM);
+    g_tab3_used = count > 0;
+    g_table_dirty = true;
+    return DBCSR_OK;
+}
 
 int smm_set_table(const int* m, const int* n, const int* variant, int count) {
     std::vector<signed char> t(TDIM * TDIM, -1);
@@ -570,49 +646,69 @@ int smm_set_table(const int* m, const int* n, const int* variant, int count) {
             return fail(DBCSR_ERR_ARG, "set_tuning: entry " + std::to_string(q) + " out of range");
         t[m[q] * TDIM + n[q]] = (signed char)variant[q];
     }
-    g_table = t;
+    std::copy(t.begin(), t.end(), g_table.begin());
     g_table_used = count > 0;
+    g_table_dirty = true;
     return DBCSR_OK;
+}
+
+int smm_table_team_bound(const std::vector<int>& ms, const std::vector<int>& ns, const std::vector<int>& ks) {
+    if (!g_table_used && !g_tab3_used) return 0;
+    if ((double)ms.size() * (double)ns.size() * (double)(ks.size() + 1) > 4e6) return 2;
+    // the classify kernel's choice for every (m, n) and inner size k of a first
+    // product: the (m, n, k) entry where set, else the (m, n) entry, else 0
+    int best = 0;
+    for (int m : ms)
+        for (int n : ns) {
+            if (m >= TDIM || n >= TDIM) continue;   // untuned: variant 0
+            const int vmn = std::max<int>(0, g_table[m * TDIM + n]);
+            for (int k : ks) {
+                int v = vmn;
+                if (g_tab3_used && m < KDIM && n < KDIM && k < KDIM) {
+                    const int t3 = g_table[TDIM * TDIM + (m * KDIM + n) * KDIM + k];
+                    if (t3 >= 0) v = t3;
+                }
+                best = std::max(best, team_of(v));
+            }
+            if (best == 2) return 2;
+        }
+    return best;
 }
 
 int smm_fp64_generic(const SmmArgs& g, int max_mn) {
     if (g.nC == 0) return DBCSR_OK;
-    return launch_all(g, max_mn, nullptr, SmmGroups{nullptr, g.nC, g.counter});
+    return launch_all(g, max_mn, nullptr, SmmGroups{nullptr, g.nC, g.counter, 0});
 }
 
-// kernel: 0 = tuned table (variant 0 for untuned shapes), v >= 1 = force variant v-1.
-// One launch: C blocks grouped by team size on the device, see k_smm_fp64_all.
-int smm_fp64_dispatch(const SmmArgs& g, int max_mn, int kernel) {
+// kernel: 0 = tuned tables (variant 0 for untuned shapes), v >= 1 = force variant v-1.
+// One launch of the product kernel; with teams of two or four warps possible,
+// a classify pass first partitions the C blocks by team size on the device.
+int smm_fp64_dispatch(const SmmArgs& g, int max_mn, int kernel, int team_bound) {
     if (g.nC == 0) return DBCSR_OK;
     if (kernel < 0 || kernel > SMM_NUM_VARIANTS) return fail(DBCSR_ERR_ARG, "unknown stack kernel variant");
     if (g.nC >= INT32_MAX) return fail(DBCSR_ERR_OVERFLOW, "stack kernels: too many C blocks");
-    const bool use_table = kernel == 0 && g_table_used;
+    const bool use_table = kernel == 0 && (g_table_used || g_tab3_used) && team_bound > 0;
     const int forced = kernel >= 1 ? kernel - 1 : -1;
     if (!use_table && (forced < 0 || kTeamWarps[forced] == 1))
-        return launch_all(g, max_mn, nullptr, SmmGroups{nullptr, g.nC, g.counter});
+        return launch_all(g, max_mn, nullptr, SmmGroups{nullptr, g.nC, g.counter, 0});
     cudaStream_t st = ctx().stream;
-    DBuf<signed char> table;
-    DBuf<uint32_t> key, idx;
-    DBuf<int> counts;
-    DBuf<unsigned long long> ctr;
-    if (use_table) {
-        DB_TRY(table.alloc(TDIM * TDIM));
-        DB_CUDA(cudaMemcpyAsync(table.p, g_table.data(), TDIM * TDIM, cudaMemcpyHostToDevice, st));
-    }
-    DB_TRY(key.alloc(g.nC));
-    DB_TRY(idx.alloc(g.nC));
-    DB_TRY(counts.alloc(3));
-    DB_TRY(ctr.alloc(3));
-    DB_CUDA(cudaMemsetAsync(counts.p, 0, sizeof(int) * 3, st));
-    DB_CUDA(cudaMemsetAsync(ctr.p, 0, sizeof(unsigned long long) * 3, st));
-    k_classify_team<<<(unsigned)cdiv(g.nC, 256), 256, 0, st>>>(g.nC, g.c_row, g.c_col, g.c_pstart, g.rsC, g.csC,
-                                                               use_table ? table.p : nullptr, TDIM, forced, key.p,
-                                                               idx.p, counts.p);
+    const signed char* table = nullptr;
+    if (use_table) DB_TRY(device_table(&table));
+    DBuf<uint32_t> lists;
+    DBuf<unsigned long long> grp;   // [0, 3): work counters; [3, 5): counts (int)
+    DB_TRY(lists.alloc((size_t)3 * g.nC));
+    DB_TRY(grp.alloc(5));
+    DB_CUDA(cudaMemsetAsync(grp.p, 0, sizeof(unsigned long long) * 5, st));
+    int* counts = reinterpret_cast<int*>(grp.p + 3);
+    k_classify_team<<<(unsigned)cdiv(g.nC, 256), 256, 0, st>>>(
+        g.nC, g.c_row, g.c_col, g.c_pstart, g.rsC, g.csC, table, TDIM,
+        (table && g_tab3_used) ? table + TDIM * TDIM : nullptr, KDIM, g.prod, g.A.off, forced, lists.p, counts);
     DB_KCHECK();
-    // stable sort by team size: each group's blocks keep CSR order (a forced
-    // variant gives one group in CSR order: no sort)
-    if (use_table) DB_TRY(radix_sort_u32(key.p, idx.p, g.nC, 8));
-    return launch_all(g, max_mn, use_table ? idx.p : nullptr, SmmGroups{counts.p, 0, ctr.p});
+    if (table) {
+        DB_CUDA(cudaEventRecord(g_table_ev, st));
+        g_table_ev_pending = true;
+    }
+    return launch_all(g, max_mn, lists.p, SmmGroups{counts, 0, grp.p, g.nC});
 }
 
 int to_f32(const double* in, int64_t n, float* out) {

@@ -68,6 +68,7 @@ SIGNATURES = [
     ("dbcsr_multiply", C.c_int, [C.c_char, C.c_char, C.c_double, _P, _P, C.c_double, _P, C.POINTER(Opts)]),
     ("dbcsr_get_stats", C.c_int, [C.POINTER(Stats)]),
     ("dbcsr_set_tuning", C.c_int, [_IP, _IP, _IP, C.c_int]),
+    ("dbcsr_set_tuning_mnk", C.c_int, [_IP, _IP, _IP, _IP, C.c_int]),
     ("dbcsr_get_stacks", C.c_int, [C.c_char, C.c_char, _P, _P, C.c_int, _IP, C.c_int64, _LP]),
     ("dbcsr_dgemm_emulated_noalloc", C.c_int, [C.c_int64, C.c_int64, C.c_int64, C.c_double, _P, C.c_int64, _P,
                                                C.c_int64, C.c_double, _P, C.c_int64, C.c_int, _P]),
@@ -302,6 +303,15 @@ def set_tuning(entries):
     e = np.asarray(list(entries), np.int32).reshape(-1, 3)
     m, n, v = (np.ascontiguousarray(e[:, q]) for q in range(3))
     _check(load().dbcsr_set_tuning(_ip(m), _ip(n), _ip(v), len(e)))
+
+
+def set_tuning_mnk(entries):
+    """FP64 stack-kernel variant per (m, n, k): iterable of (m, n, k, variant), all
+    sizes 1..32; k is the inner size of a C block's first product. An empty
+    iterable clears the table."""
+    e = np.asarray(list(entries), np.int32).reshape(-1, 4)
+    m, n, k, v = (np.ascontiguousarray(e[:, q]) for q in range(4))
+    _check(load().dbcsr_set_tuning_mnk(_ip(m), _ip(n), _ip(k), _ip(v), len(e)))
 
 
 def stats() -> dict:

@@ -238,6 +238,15 @@ class PerfModel:
                 out.append((int(m), int(n), int(np.argmax(p)), float(p.max())))
         return out
 
+    def table_mnk(self, msizes, nsizes, ksizes) -> list[tuple[int, int, int, int, float]]:
+        """(m, n, k, variant, predicted TFLOP/s) entries for dbcsr_set_tuning_mnk: the
+        predicted best variant of every (m, n, k) shape."""
+        nv = len(VARIANTS)
+        shapes = [(int(m), int(n), int(k)) for m in msizes for n in nsizes for k in ksizes]
+        X = np.stack([features(m, n, k, v) for (m, n, k) in shapes for v in range(nv)])
+        p = self.forest.predict(X).reshape(len(shapes), nv)
+        return [(m, n, k, int(np.argmax(p[i])), float(p[i].max())) for i, (m, n, k) in enumerate(shapes)]
+
 
 def choice_quality(measured: dict, chosen: dict) -> dict:
     """How good a per-shape choice is against the measured optimum.

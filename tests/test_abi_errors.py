@@ -75,6 +75,8 @@ def test_null_handles_rejected(L):
         (lambda: L.dbcsr_get_stats(None), "get_stats: NULL"),
         (lambda: L.dbcsr_set_tuning(None, None, None, -1), "set_tuning: bad arguments"),
         (lambda: L.dbcsr_set_tuning(None, None, None, 3), "set_tuning: bad arguments"),
+        (lambda: L.dbcsr_set_tuning_mnk(None, None, None, None, 3), "set_tuning_mnk: bad arguments"),
+        (lambda: L.dbcsr_set_tuning_mnk(None, None, None, None, -1), "set_tuning_mnk: bad arguments"),
     ]
     for call, msg in checks:
         assert call() == dbcsr.ERR_ARG, msg
@@ -119,3 +121,12 @@ def test_binding_allocator_hooks_come_in_pairs(L):
     with pytest.raises(ValueError):
         dbcsr.set_allocator(None, lambda ptr, nbytes, stream: None)
     dbcsr.set_allocator(None, None)   # the built-in pool: accepted without a GPU
+
+
+def test_tuning_mnk_entries_out_of_range(L):
+    # m, n, k in 1..32 and variant in 0..3 (host checks, no GPU needed)
+    for bad in ([33, 5, 5, 0], [5, 0, 5, 0], [5, 5, 40, 0], [5, 5, 5, 4], [5, 5, 5, -1]):
+        a = [np.array([x], np.int32) for x in bad]
+        assert L.dbcsr_set_tuning_mnk(*[_ip(x) for x in a], 1) == dbcsr.ERR_ARG
+        assert "out of range" in last(L)
+    assert L.dbcsr_set_tuning_mnk(None, None, None, None, 0) == dbcsr.OK   # clears the table

@@ -5,7 +5,10 @@ DBCSR_PATH_AUTO, a sparse multiply in emulated FP64 with a block edge above 32
 (the emulated stack kernels' limit), and TF32 on sparse operands (no TF32
 stack kernel), take the densified GEMM of Sec. III and return the result on
 the symbolic pattern; they are not refused. FP64 keeps the stack kernels,
-which take any block size.
+which take any block size. Fully occupied operands take the densified GEMM
+(Sec. III), except FP32 (no FP32 dense path) and FP64 with every block edge up
+to 32, which stay on the stack kernels (measured faster there than the FP64
+tensor-core GEMM).
 """
 import numpy as np
 import pytest
@@ -72,3 +75,24 @@ def test_auto_tf32_sparse_takes_dense():
                                        O.undensify(O.round_tf32(Ad) @ O.round_tf32(Bd) + 0.5 * O.densify(Cm),
                                                    ref.row_sizes, ref.col_sizes, ref.blk_row, ref.blk_col)))
     assert O.normwise_error(O.densify(got), want, Ad, Bd) <= 2e-6
+
+
+@pytest.mark.parametrize("precision,bs,path", [("fp64", 22, dbcsr.PATH_STACKS), ("fp64", 32, dbcsr.PATH_STACKS),
+                                               ("fp64", 33, dbcsr.PATH_DENSE), ("ozaki", 22, dbcsr.PATH_DENSE),
+                                               ("tf32", 22, dbcsr.PATH_DENSE)])
+def test_auto_fully_occupied(precision, bs, path):
+    rng = np.random.default_rng(1000 + bs)
+    A = synth.dense_matrix(rng, 6, 5, bs, bs)
+    B = synth.dense_matrix(rng, 5, 7, bs, bs)
+    Cm = synth.dense_matrix(rng, 6, 7, bs, bs)
+    got, st = gpu_multiply("N", "N", 1.0, A, B, 0.5, Cm, path="auto", precision=precision)
+    assert st["path"] == path
+    if precision == "ozaki":
+        ref = emul_ref(A, B, Cm, 1.0, 0.5)
+        assert_same_pattern(got, ref)
+        assert np.array_equal(got.data, ref.data)
+        return
+    ref = O.multiply("N", "N", 1.0, A, B, 0.5, Cm)
+    assert_same_pattern(got, ref)
+    err = O.normwise_error(O.densify(got), O.densify(ref), O.densify(A), O.densify(B))
+    assert err <= (1e-13 if precision == "fp64" else 1e-2)

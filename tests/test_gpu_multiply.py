@@ -99,9 +99,11 @@ def test_dense_path_ragged_tiles(nb, bs):
     A = synth.dense_matrix(rng, nb, nb + 2, bs, bs)
     B = synth.dense_matrix(rng, nb + 2, nb + 1, bs, bs)
     Cm = synth.dense_matrix(rng, nb, nb + 1, bs, bs)
-    _, _, st = check("N", "N", 1.0, A, B, 1.0, Cm)
+    _, _, st = check("N", "N", 1.0, A, B, 1.0, Cm, path="dense")
     assert st["path"] == dbcsr.PATH_DENSE
-    check("N", "N", 1.0, A, B, 1.0, Cm, path="stacks")
+    # FP64 blocks up to 32 x 32 stay on the stack kernels under AUTO
+    _, _, st = check("N", "N", 1.0, A, B, 1.0, Cm)
+    assert st["path"] == dbcsr.PATH_STACKS
 
 
 def test_uneven_banded_small():

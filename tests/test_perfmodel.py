@@ -101,3 +101,31 @@ def test_choice_quality_arithmetic():
     q = P.choice_quality(measured, {(1, 1, 1): 0, (2, 2, 2): 0})
     assert q["mean_of_best"] == pytest.approx(0.75) and q["min_of_best"] == pytest.approx(0.5)
     assert q["optimal"] == 0.5 and q["within_5pct"] == 0.5
+
+
+def test_table_mnk_matches_best_variant():
+    # per-(m, n, k) entries are the model's argmax on every shape; the (m, n)
+    # table averages over k and can differ from them
+    sizes = (4, 8, 16, 32)
+    recs = [(m, n, k, v, _synthetic_perf(m, n, k, v)) for m in sizes for n in sizes for k in sizes
+            for v in range(4)]
+    model = P.PerfModel(P.RandomForest(n_trees=5, seed=1)).fit(recs)
+    tab = model.table_mnk((4, 13), (8,), (2, 32))
+    assert [e[:3] for e in tab] == [(4, 8, 2), (4, 8, 32), (13, 8, 2), (13, 8, 32)]
+    for (m, n, k, v, t) in tab:
+        assert v == model.best_variant(m, n, k)
+        assert t == pytest.approx(model.predict(m, n, k).max())
+
+
+def test_mnk_table_string_roundtrip():
+    from paper_1910_04796_gb300 import autotune
+    E = 5
+    rng = np.random.default_rng(4)
+    entries = [(m, n, k, int(rng.integers(0, 4))) for m in range(1, E + 1) for n in range(1, E + 1)
+               for k in range(1, E + 1)]
+    code = autotune.encode_mnk(entries, E)
+    assert len(code) == E ** 3 and set(code) <= set("0123")
+    # the stated index: ((m-1)*E + (n-1))*E + (k-1)
+    m, n, k, v = entries[37]
+    assert code[((m - 1) * E + (n - 1)) * E + (k - 1)] == str(v)
+    assert autotune.decode_mnk(code, E) == entries
