@@ -51,27 +51,35 @@ def peaks():
 TRAFFIC_TABLE = os.path.join(ROOT, "profiles", "dram_traffic.md")
 
 
-def dram_traffic(workload_name, precision, path):
-    """DRAM bytes (read + write) per launch of the dominant kernel, from the ncu
-    capture recorded in profiles/dram_traffic.md; None unless the kernel's
-    source file is unchanged since (its SHA-256 is recorded with the number)."""
+def traffic_rows(precision, path):
+    """{workload: DRAM bytes (read + write) per launch of the dominant kernel}
+    from the ncu captures recorded in profiles/dram_traffic.md, for rows whose
+    kernel source file is unchanged since (its SHA-256 is recorded with the
+    number)."""
     import hashlib
     try:
         lines = open(TRAFFIC_TABLE).read().splitlines()
     except OSError:
-        return None
+        return {}
+    out = {}
     for ln in lines:
         cells = [c.strip() for c in ln.strip().strip("|").split("|")]
-        if len(cells) != 7 or cells[0] != workload_name or cells[1] != precision or cells[2] != path:
+        if len(cells) != 7 or cells[1] != precision or cells[2] != path:
             continue
         try:
             with open(os.path.join(ROOT, cells[4]), "rb") as f:
                 if hashlib.sha256(f.read()).hexdigest() != cells[5]:
-                    return None
-            return float(cells[6])
+                    continue
+            out[cells[0]] = float(cells[6])
         except (OSError, ValueError):
-            return None
-    return None
+            continue
+    return out
+
+
+def dram_traffic(workload_name, precision, path):
+    """DRAM bytes per launch of the dominant kernel on this workload, or None
+    (no capture of it, or the kernel changed since)."""
+    return traffic_rows(precision, path).get(workload_name)
 
 
 def workload(name, scale, occ=0.1):
@@ -141,7 +149,7 @@ class Clocks:
                 self.proc.kill()
 
     def summary(self):
-        sm, mx, reasons = [], [], set()
+        sm, mx, pw, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
@@ -152,13 +160,17 @@ class Clocks:
                 mx.append(float(f[1]))
             except ValueError:
                 continue
+            try:
+                pw.append(float(f[2]))
+            except ValueError:
+                pass
             for n, v in zip(names, f[3:7]):
                 if v.lower() == "active":
                     reasons.add(n)
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "power_w": statistics.median(pw) if pw else None}
 
 
 def dist_setup(args):
@@ -383,7 +395,12 @@ def main():
         peak_note = f"TF32 = {pk_kind} bf16 burst x nominal TF32/bf16 (1100/2250)"
         achieved = s2["main_flops"] / (main_ms / 1e3) / 1e12
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": unit, "frac": achieved / peak,
-                "traffic": dram_traffic(w.name, precision, path_taken), "kernel_ms": main_ms,
+                "traffic": dram_traffic(w.name, precision, path_taken),
+                # captures of smaller cases of the same kernel (their own workloads;
+                # traffic does not grow in proportion to the work, so none is scaled)
+                "traffic_small_cases": {k: v for k, v in traffic_rows(precision, path_taken).items()
+                                        if k != w.name} or None,
+                "kernel_ms": main_ms,
                 "algorithmic_flops": s2["main_flops"], "peak_source": peak_note}
 
     # end to end through the C ABI with host buffers (H2D of inputs and D2H of C inside);

@@ -44,6 +44,25 @@ def test_traffic_reported_only_for_the_recorded_source(tmp_path, monkeypatch):
     assert bench.dram_traffic("w-small", "ozaki", "dense") is None
 
 
+def test_small_case_rows_listed_apart(tmp_path, monkeypatch):
+    # captures of smaller cases of the same kernel are listed by workload; none
+    # stands in for another workload's number
+    src = tmp_path / "kernel.cu"
+    src.write_bytes(b"k")
+    sha = hashlib.sha256(b"k").hexdigest()
+    t = tmp_path / "traffic.md"
+    t.write_text("| workload | precision | path | kernel | source | sha256 | dram bytes per launch |\n"
+                 "|---|---|---|---|---|---|---|\n"
+                 f"| w-a | ozaki | dense | k_x | kernel.cu | {sha} | 10 |\n"
+                 f"| w-b | ozaki | dense | k_x | kernel.cu | {sha} | 20 |\n"
+                 f"| w-c | fp64 | dense | k_x | kernel.cu | {sha} | 30 |\n"
+                 f"| w-d | ozaki | dense | k_x | kernel.cu | {'0' * 64} | 40 |\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "TRAFFIC_TABLE", str(t))
+    assert bench.traffic_rows("ozaki", "dense") == {"w-a": 10.0, "w-b": 20.0}
+    assert bench.dram_traffic("w-full", "ozaki", "dense") is None
+
+
 def test_traffic_missing_or_malformed_gives_none(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     monkeypatch.setattr(bench, "TRAFFIC_TABLE", str(tmp_path / "absent.md"))
@@ -77,7 +96,8 @@ def test_clock_summary():
         "[N/A], 2070, 1, Not Active, Not Active, Not Active, Not Active",
     ]
     s = c.summary()
-    assert s == {"sm_mhz": 1965.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    assert s == {"sm_mhz": 1965.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3,
+                 "power_w": 1180.2}
     c.lines.append("1200, 2070, 900.0, Active, Not Active, Active, Not Active")
     assert c.summary()["reasons"] == ["hw_slowdown", "sw_power_cap", "sw_thermal_slowdown"]
     empty = bench.Clocks()
