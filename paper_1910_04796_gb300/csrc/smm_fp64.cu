@@ -267,22 +267,25 @@ __global__ void __launch_bounds__(256, Q <= 16 ? 2 : 1) k_smm_fp32(SmmArgs g, co
 
 // FP32 stack kernel for blocks up to 32 x 32: a warp per C block; each
 // product's op(A) and op(B) blocks are staged in the warp's shared memory
-// (A(i, l) at l * 36 + i, B(l, j) at l * 36 + j: rows 16-byte aligned), and
-// each lane computes an R x CC patch of the C block held in registers: per
+// (A(i, l) at l * SA + i, B(l, j) at l * SB + j, with SA and SB the block's
+// padded row and column counts (8, 16 or 32) plus 4: rows 16-byte aligned),
+// and each lane computes an R x CC patch of the C block held in registers: per
 // inner index l it loads R values of A's column l and CC values of B's row l
-// (vector loads) and issues R * CC FMAs. The patch shape follows the block's
-// padded size (8, 16 or 32 per dimension), so that all 32 lanes carry work:
-// 8 x 4 patches for 32 x 32 blocks (32 FMAs per three vector loads), down to
-// 2 x 1 for 8 x 8. FMA order per element: products in plan order, l
-// ascending. Two staging buffers per warp: the asynchronous copies (cp.async,
-// 4 bytes each) of the next product's blocks run while the current one is
-// computed. Patch rows from m and columns from n read whatever the staging
-// buffer holds there and feed accumulators that are never stored.
+// (vector loads) and issues R * CC FMAs. The patch shape follows the padded
+// size, so that all 32 lanes carry work: 8 x 4 patches for 32 x 32 blocks (32
+// FMAs per three vector loads), down to 2 x 1 for 8 x 8. FMA order per
+// element: products in plan order, l ascending. The warp's staging space holds
+// NS stages of the padded size (2 for 32 x 32 blocks, up to 6 for 8 x 8): the
+// asynchronous copies (cp.async, 4 bytes each) of the next NS - 1 products run
+// while the current one is computed. The products' operand offsets and inner
+// sizes are read 32 at a time, one product per lane, and passed on by warp
+// shuffles, so no dependent global load sits between two products. Patch rows
+// from m and columns from n read whatever the staging buffer holds there and
+// feed accumulators that are never stored.
 constexpr int F32_WARPS = 4;
-constexpr int F32_STRIDE = 36;   // floats per staged row of A (per l) and of B (per l)
-constexpr int F32_BUF_FLOATS = 2 * 32 * F32_STRIDE;   // A, B
-constexpr int F32_WARP_FLOATS = 2 * F32_BUF_FLOATS;
+constexpr int F32_WARP_FLOATS = 2 * 2 * 32 * 36;   // two stages of 32 x 32 blocks (A and B, rows of 36)
 constexpr int F32_SMEM = F32_WARPS * F32_WARP_FLOATS * (int)sizeof(float);
+constexpr int F32_MAX_STAGES = 6;
 
 __device__ __forceinline__ void cp_async4(float* dst, const float* src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
@@ -291,25 +294,26 @@ __device__ __forceinline__ void cp_async4(float* dst, const float* src) {
 }
 
 // the copies of one product's op(A) (m x kk) and op(B) (kk x n) blocks into a
-// staging buffer; the lane runs along the contiguous index of each stored block
-template <int TA, int TB>
+// staging buffer (row strides SA, SB); the lane runs along the contiguous index
+// of each stored block
+template <int TA, int TB, int SA, int SB>
 __device__ __forceinline__ void f32_stage(const float* ga, const float* gb, int m, int n, int kk, float* a_s,
                                           float* b_s, int lane) {
     // op(A): element (i, l) of the stored block at i + l*m (TA = 0) or l + i*kk (TA = 1)
     if (!TA) {
         if (lane < m)
-            for (int l = 0; l < kk; l++) cp_async4(a_s + l * F32_STRIDE + lane, ga + lane + l * m);
+            for (int l = 0; l < kk; l++) cp_async4(a_s + l * SA + lane, ga + lane + l * m);
     } else {
         if (lane < kk)
-            for (int i = 0; i < m; i++) cp_async4(a_s + lane * F32_STRIDE + i, ga + lane + i * kk);
+            for (int i = 0; i < m; i++) cp_async4(a_s + lane * SA + i, ga + lane + i * kk);
     }
     // op(B): element (l, j) at l + j*kk (TB = 0) or j + l*n (TB = 1)
     if (!TB) {
         if (lane < kk)
-            for (int j = 0; j < n; j++) cp_async4(b_s + lane * F32_STRIDE + j, gb + lane + j * kk);
+            for (int j = 0; j < n; j++) cp_async4(b_s + lane * SB + j, gb + lane + j * kk);
     } else {
         if (lane < n)
-            for (int l = 0; l < kk; l++) cp_async4(b_s + l * F32_STRIDE + lane, gb + lane + l * n);
+            for (int l = 0; l < kk; l++) cp_async4(b_s + l * SB + lane, gb + lane + l * n);
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
@@ -329,10 +333,15 @@ __device__ __forceinline__ void f32_load(const float* p, float (&v)[X]) {
     }
 }
 // one C block (m x n, both at most 32) on one warp with R x CC patches, LC
-// lanes across the columns and 32 / LC down the rows
-template <int TA, int TB, int R, int CC, int LC>
-__device__ __forceinline__ void f32_cblock(const SmmArgs& g, int64_t cb, int m, int n, float* wbuf, int lane,
-                                           const BlasUpd& bu) {
+// lanes across the columns and 32 / LC down the rows; rows padded to RP and
+// columns to CP in the staging buffers. skk: the warp's inner size per stage.
+template <int TA, int TB, int R, int CC, int LC, int RP, int CP>
+__device__ __forceinline__ void f32_cblock(const SmmArgs& g, int64_t cb, int m, int n, float* wbuf, int* skk,
+                                           int lane, const BlasUpd& bu) {
+    constexpr int SA = RP + 4, SB = CP + 4;
+    constexpr int STAGE = 32 * (SA + SB);
+    constexpr int NS = F32_WARP_FLOATS / STAGE < F32_MAX_STAGES ? F32_WARP_FLOATS / STAGE : F32_MAX_STAGES;
+    static_assert(NS >= 2, "two stages at least");
     const int row0 = (lane / LC) * R, col0 = (lane % LC) * CC;
     const int64_t p0 = g.c_pstart[cb], p1 = g.c_pstart[cb + 1];
     float acc[R][CC];
@@ -340,49 +349,60 @@ __device__ __forceinline__ void f32_cblock(const SmmArgs& g, int64_t cb, int m, 
     for (int r = 0; r < R; r++)
 #pragma unroll
         for (int c = 0; c < CC; c++) acc[r][c] = 0.f;
-    // operands of product p: offsets and inner size
-    auto operands = [&](int64_t p, const float*& ga, const float*& gb, int& kk) {
-        const int2 pr = g.prod[p];
-        const int64_t ao = g.A.off[pr.x], bo = g.B.off[pr.y];
-        kk = (int)(g.A.off[pr.x + 1] - ao) / m;
-        ga = g.A32 + ao;
-        gb = g.B32 + bo;
-    };
-    const float *ga = nullptr, *gb = nullptr;
-    int kk = 0;
-    if (p0 < p1) {
-        operands(p0, ga, gb, kk);
-        f32_stage<TA, TB>(ga, gb, m, n, kk, wbuf, wbuf + 32 * F32_STRIDE, lane);
-    }
-    for (int64_t p = p0; p < p1; p++) {
-        const int cur_kk = kk;
-        const float* a_s = wbuf + ((p - p0) & 1) * F32_BUF_FLOATS;
-        const float* b_s = a_s + 32 * F32_STRIDE;
-        if (p + 1 < p1) {
-            // the other buffer was last read by product p - 1, finished by every lane
-            __syncwarp();
-            operands(p + 1, ga, gb, kk);
-            float* na = wbuf + ((p + 1 - p0) & 1) * F32_BUF_FLOATS;
-            f32_stage<TA, TB>(ga, gb, m, n, kk, na, na + 32 * F32_STRIDE, lane);
-            asm volatile("cp.async.wait_group 1;" ::: "memory");
-        } else {
-            asm volatile("cp.async.wait_group 0;" ::: "memory");
+    // descriptors of products pbase .. pbase + 31, one per lane
+    int64_t pbase = p0 - 32, d_ao = 0, d_bo = 0;
+    int d_kk = 0;
+    // stage product p (products are staged once each, in ascending order) into slot s
+    auto stage = [&](int64_t p, int s) {
+        if (p >= pbase + 32) {
+            pbase = p;
+            const int64_t q = p + lane;
+            if (q < p1) {
+                const int2 pr = g.prod[q];
+                d_ao = g.A.off[pr.x];
+                d_kk = (int)((g.A.off[pr.x + 1] - d_ao) / m);
+                d_bo = g.B.off[pr.y];
+            }
         }
+        const int src = (int)(p - pbase);
+        const int64_t ao = __shfl_sync(0xffffffffu, d_ao, src);
+        const int64_t bo = __shfl_sync(0xffffffffu, d_bo, src);
+        const int kk = __shfl_sync(0xffffffffu, d_kk, src);
+        if (lane == 0) skk[s] = kk;
+        float* a_s = wbuf + s * STAGE;
+        f32_stage<TA, TB, SA, SB>(g.A32 + ao, g.B32 + bo, m, n, kk, a_s, a_s + 32 * SA, lane);
+    };
+#pragma unroll 1
+    for (int s = 0; s < NS - 1; s++) {
+        if (p0 + s < p1) stage(p0 + s, s);
+        else asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    int cs = 0;   // slot of product p
+#pragma unroll 1
+    for (int64_t p = p0; p < p1; p++) {
+        // slot cs - 1 (mod NS) was last read by product p - 1, finished by every lane
+        __syncwarp();
+        if (p + NS - 1 < p1) stage(p + NS - 1, cs == 0 ? NS - 1 : cs - 1);
+        else asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group %0;" ::"n"(NS - 1) : "memory");
         __syncwarp();   // product p's blocks are in shared memory for every lane
-        const float* ar = a_s + row0;
-        const float* bc = b_s + col0;
+        const int cur_kk = skk[cs];
+        const float* ar = wbuf + cs * STAGE + row0;
+        const float* bc = wbuf + cs * STAGE + 32 * SA + col0;
 #pragma unroll 2
         for (int l = 0; l < cur_kk; l++) {
             float av[R], bv[CC];
-            f32_load<R>(ar + l * F32_STRIDE, av);
-            f32_load<CC>(bc + l * F32_STRIDE, bv);
+            f32_load<R>(ar + l * SA, av);
+            f32_load<CC>(bc + l * SB, bv);
 #pragma unroll
             for (int r = 0; r < R; r++)
 #pragma unroll
                 for (int c = 0; c < CC; c++) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
         }
+        cs = cs + 1 == NS ? 0 : cs + 1;
     }
-    __syncwarp();   // the next C block's first copies overwrite buffer 0
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncwarp();   // the next C block's first copies overwrite the slots
     // alpha / beta in FP64, column-major C block
     double* cout = g.Cd + g.c_off[cb];
     const int o = g.c_old ? g.c_old[cb] : -1;
@@ -417,12 +437,14 @@ __global__ void k_f32_classify(int64_t nC, const int* __restrict__ c_row, const 
 }
 
 template <int TA, int TB>
-__global__ void __launch_bounds__(32 * F32_WARPS) k_smm_f32_tile(SmmArgs g, const uint32_t* __restrict__ order,
+__global__ void __launch_bounds__(32 * F32_WARPS, 3) k_smm_f32_tile(SmmArgs g, const uint32_t* __restrict__ order,
                                                                  int chunk) {
     extern __shared__ __align__(16) float f32_smem[];
     __shared__ int s_cb[F32_WARPS];
+    __shared__ int s_kk[F32_WARPS][F32_MAX_STAGES];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float* wbuf = f32_smem + warp * F32_WARP_FLOATS;
+    int* skk = s_kk[warp];
     const BlasUpd bu(g.alpha, g.beta);
     for (;;) {
         if (lane == 0) s_cb[warp] = (int)atomicAdd(g.counter, (unsigned long long)chunk);
@@ -436,15 +458,15 @@ __global__ void __launch_bounds__(32 * F32_WARPS) k_smm_f32_tile(SmmArgs g, cons
             const int m = g.rsC[g.c_row[cb]], n = g.csC[g.c_col[cb]];
             // patch shape by padded size (rows 8 / 16 / 32) x (columns 8 / 16 / 32)
             switch (f32_class(m) * 3 + f32_class(n)) {
-                case 0: f32_cblock<TA, TB, 2, 1, 8>(g, cb, m, n, wbuf, lane, bu); break;   //  8 x  8
-                case 1: f32_cblock<TA, TB, 2, 2, 8>(g, cb, m, n, wbuf, lane, bu); break;   //  8 x 16
-                case 2: f32_cblock<TA, TB, 2, 4, 8>(g, cb, m, n, wbuf, lane, bu); break;   //  8 x 32
-                case 3: f32_cblock<TA, TB, 2, 2, 4>(g, cb, m, n, wbuf, lane, bu); break;   // 16 x  8
-                case 4: f32_cblock<TA, TB, 4, 2, 8>(g, cb, m, n, wbuf, lane, bu); break;   // 16 x 16
-                case 5: f32_cblock<TA, TB, 4, 4, 8>(g, cb, m, n, wbuf, lane, bu); break;   // 16 x 32
-                case 6: f32_cblock<TA, TB, 4, 2, 4>(g, cb, m, n, wbuf, lane, bu); break;   // 32 x  8
-                case 7: f32_cblock<TA, TB, 4, 4, 4>(g, cb, m, n, wbuf, lane, bu); break;   // 32 x 16
-                default: f32_cblock<TA, TB, 8, 4, 8>(g, cb, m, n, wbuf, lane, bu); break;  // 32 x 32
+                case 0: f32_cblock<TA, TB, 2, 1, 8, 8, 8>(g, cb, m, n, wbuf, skk, lane, bu); break;
+                case 1: f32_cblock<TA, TB, 2, 2, 8, 8, 16>(g, cb, m, n, wbuf, skk, lane, bu); break;
+                case 2: f32_cblock<TA, TB, 2, 4, 8, 8, 32>(g, cb, m, n, wbuf, skk, lane, bu); break;
+                case 3: f32_cblock<TA, TB, 2, 2, 4, 16, 8>(g, cb, m, n, wbuf, skk, lane, bu); break;
+                case 4: f32_cblock<TA, TB, 4, 2, 8, 16, 16>(g, cb, m, n, wbuf, skk, lane, bu); break;
+                case 5: f32_cblock<TA, TB, 4, 4, 8, 16, 32>(g, cb, m, n, wbuf, skk, lane, bu); break;
+                case 6: f32_cblock<TA, TB, 4, 2, 4, 32, 8>(g, cb, m, n, wbuf, skk, lane, bu); break;
+                case 7: f32_cblock<TA, TB, 4, 4, 4, 32, 16>(g, cb, m, n, wbuf, skk, lane, bu); break;
+                default: f32_cblock<TA, TB, 8, 4, 8, 32, 32>(g, cb, m, n, wbuf, skk, lane, bu); break;
             }
         }
     }

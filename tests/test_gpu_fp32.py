@@ -48,6 +48,22 @@ def test_fp32_small_integers_bit_exact():
     assert np.array_equal(got.data, O.multiply("N", "N", 1.0, A, B, 0.0, mode=2).data)
 
 
+@pytest.mark.parametrize("ta,tb", [("N", "N"), ("T", "T")])
+def test_fp32_long_product_lists_every_class_bit_exact(ta, tb):
+    # C blocks of every patch class (edges 5, 13 and 32, padded to 8, 16 and 32)
+    # with about 50 products each: the products' operand offsets are read 32 at
+    # a time and the staging ring runs 2 to 6 stages deep. Small integers: the
+    # FP32 sums are exact, so any order of them gives the oracle's bits.
+    rng = np.random.default_rng(905)
+    A, B, Cm = synth.random_small(rng, 9, 72, 9, p=0.7, sizes=(5, 13, 32), dist="int", with_c=True, c_p=0.6)
+    As = synth.transpose_blocks(A) if ta == "T" else A
+    Bs = synth.transpose_blocks(B) if tb == "T" else B
+    got, _ = gpu_multiply(ta, tb, 1.0, As, Bs, 1.0, Cm, path="stacks", precision="fp32")
+    ref = O.multiply(ta, tb, 1.0, As, Bs, 1.0, Cm, mode=2)
+    assert_same_pattern(got, ref)
+    assert np.array_equal(got.data, ref.data)
+
+
 def test_fp32_larger_grid_and_error_vs_fp64():
     w = synth.workload_small_sparse(0)
     got, _ = gpu_multiply("N", "N", 1.0, w.A, w.B, 0.0, path="stacks", precision="fp32")
