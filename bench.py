@@ -414,28 +414,40 @@ def main():
         hOut = pin(np.zeros(max(1, int(Cm.info()[3])), np.float64))
         out = None
 
+        phases = []   # host time per step of the creates, the multiply and the read-back
+
         def e2e_step():
             nonlocal out
+            t0 = time.perf_counter()
             Ah = dbcsr.Matrix.create(w.A.row_sizes, w.A.col_sizes, w.A.blk_row, w.A.blk_col, hA)
             Bh = dbcsr.Matrix.create(w.B.row_sizes, w.B.col_sizes, w.B.blk_row, w.B.blk_col, hB)
             if C0 is not None:
                 Ch = dbcsr.Matrix.create(C0.row_sizes, C0.col_sizes, C0.blk_row, C0.blk_col, hC)
             else:
                 Ch = dbcsr.Matrix.create(rs, cs, np.zeros(0, np.int32), np.zeros(0, np.int32))
+            t1 = time.perf_counter()
             dbcsr.multiply(w.transa, w.transb, w.alpha, Ah, Bh, w.beta, Ch, path=args.path, precision=precision,
                            ozaki_slices=args.slices, kernel=args.kernel, hybrid_panel=hpanel,
                            hybrid_fill_pct=args.hybrid_fill)
+            t2 = time.perf_counter()
             out = Ch.data(hOut)
+            t3 = time.perf_counter()
             for m in (Ah, Bh, Ch):
                 m.release()
+            phases.append((t1 - t0, t2 - t1, t3 - t2))
 
-        e2e_steps = max(1, min(args.steps, 3))
+        e2e_steps = max(1, args.steps)
         s_e2e, _ = time_steps(e2e_step, e2e_steps, 2, world)
         s_e2e = max_over_ranks(s_e2e, world)
+        timed = phases[-e2e_steps:]
         h2d = (hA.nbytes + hB.nbytes + (hC.nbytes if hC is not None else 0)
                + 4 * 2 * (w.A.nblks + w.B.nblks + (C0.nblks if C0 is not None else 0)))
         e2e = {"value": useful * world * e2e_steps / s_e2e / 1e12, "unit": "TFLOP/s",
-               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(out.nbytes if out is not None else 0)}
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(out.nbytes if out is not None else 0),
+               # median host time of each call group per step: the creates return while
+               # page-locked values still copy, so their copies overlap the multiply
+               "phases_ms": {k: 1e3 * statistics.median(p[q] for p in timed)
+                             for q, k in enumerate(("creates", "multiply", "read_back"))}}
 
     # comparison legs on the same GPU and inputs: the plain FP64 paths, the
     # emulated and TF32 paths with their error against the GPU FP64 result

@@ -25,8 +25,13 @@
  *     the last error on the calling thread is available from dbcsr_last_error().
  *     No C++ exception ever crosses this interface.
  *   - All GPU work is ordered on the stream given to dbcsr_init() (default: the
- *     legacy default stream). Entry points that return host data synchronise
- *     that stream before returning.
+ *     legacy default stream), except the copies of matrix values from
+ *     page-locked host memory made by dbcsr_create() and dbcsr_set_data():
+ *     those run on a transfer stream of the library, so that they overlap
+ *     work already queued (Sec. II: host-to-device transfers double-buffered
+ *     against the computation with CUDA streams), and every later use of the
+ *     matrix waits for its copy. Entry points that return host data synchronise the library
+ *     stream before returning; dbcsr_sync() waits for both streams.
  *   - Device memory is obtained through the allocator set with
  *     dbcsr_set_allocator(), else from CUDA's stream-ordered pool
  *     (cudaMallocAsync on the library stream; freed blocks stay in the pool).
@@ -178,6 +183,12 @@ DBCSR_API int dbcsr_set_allocator(dbcsr_alloc_fn alloc, dbcsr_free_fn free_fn, v
  *                         memory if data_on_device == 0, device memory
  *                         otherwise; NULL creates all-zero blocks
  * The library copies everything; the caller keeps ownership of its arrays.
+ * Host values in CSR order from page-locked (pinned) memory are copied on the
+ * library's transfer stream: the call returns while they copy, the matrix's
+ * next use waits for the copy, and `data` must stay unchanged until a call
+ * that synchronises has returned (dbcsr_sync(), or any call that returns the
+ * matrix's values to the host). From pageable memory the copy is complete
+ * when the call returns.
  * Blocks are stored in CSR order (row, then column ascending). */
 DBCSR_API int dbcsr_create(dbcsr_matrix *out, int nblkrows, int nblkcols,
                  const int *row_blk_sizes, const int *col_blk_sizes,
@@ -206,11 +217,15 @@ DBCSR_API int dbcsr_get_data(dbcsr_matrix m, double *out, int out_on_device);
 
 /* Overwrite all stored values (nelems doubles, storage order) from `data`,
  * host memory if data_on_device == 0, else device memory. The pattern is
- * unchanged, so a kept stack plan (dbcsr_opts.reuse_plan) stays valid. */
+ * unchanged, so a kept stack plan (dbcsr_opts.reuse_plan) stays valid. Host
+ * values are copied as in dbcsr_create() (from page-locked memory on the
+ * transfer stream: `data` must stay unchanged until a call that synchronises
+ * has returned); device values are copied before the call returns. */
 DBCSR_API int dbcsr_set_data(dbcsr_matrix m, const double *data, int data_on_device);
 
 /* Device pointer of the stored values (valid until the next call that changes
- * the matrix) -- for callers that keep data resident on the GPU. */
+ * the matrix) -- for callers that keep data resident on the GPU. A copy of
+ * host values still in flight is waited for before the call returns. */
 DBCSR_API int dbcsr_data_ptr(dbcsr_matrix m, double **dev_ptr);
 
 /* Copy block (row, col) to host `out_colmajor` (row_blk_size x col_blk_size
@@ -309,7 +324,7 @@ DBCSR_API int dbcsr_dgemm_emulated_noalloc(int64_t M, int64_t N, int64_t K, doub
  * on any thread; not to dbcsr_dgemm_emulated_noalloc (fixed 4 s). */
 DBCSR_API int dbcsr_set_wait_limit(int64_t ns);
 
-/* Wait for all work the library queued on its stream. */
+/* Wait for all work the library queued on its stream and its transfer stream. */
 DBCSR_API int dbcsr_sync(void);
 
 /* Message of the last error on the calling thread ("" if none). */

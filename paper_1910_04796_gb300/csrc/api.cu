@@ -60,6 +60,8 @@ int ensure_device() {
     g_ctx.num_sms = sms;
     cudaError_t e = cudaMalloc(&g_ctx.d_flags, 64 * sizeof(int));
     if (e != cudaSuccess) return fail(DBCSR_ERR_ALLOC, std::string("flag buffer: ") + cudaGetErrorString(e));
+    DB_CUDA(cudaStreamCreateWithFlags(&g_ctx.xfer, cudaStreamNonBlocking));
+    DB_CUDA(cudaEventCreateWithFlags(&g_ctx.order_ev, cudaEventDisableTiming));
     g_ctx.device = dev;
     return DBCSR_OK;
 }
@@ -116,7 +118,39 @@ int sync_stream() {
     return DBCSR_OK;
 }
 
+int await_data(dbcsr_matrix_s* m) {
+    if (m && m->pending) {
+        DB_CUDA(cudaStreamWaitEvent(g_ctx.stream, m->ready, 0));
+        m->pending = false;
+    }
+    return DBCSR_OK;
+}
+
+// Copy n host values into m->d_data. From page-locked memory the copy runs
+// on the transfer stream, after everything the library stream has queued so
+// far (the allocation of d_data, earlier reads of it), and the library stream
+// waits for it at the next use of m. From pageable memory, which the copy
+// engine cannot read directly, it is done on the library stream before the
+// call returns.
+int upload_data(dbcsr_matrix_s* m, const double* data, int64_t n) {
+    DB_TRY(await_data(m));
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, data) != cudaSuccess || at.type != cudaMemoryTypeHost) {
+        cudaGetLastError();
+        DB_CUDA(cudaMemcpyAsync(m->d_data, data, sizeof(double) * n, cudaMemcpyHostToDevice, g_ctx.stream));
+        return sync_stream();
+    }
+    if (!m->ready) DB_CUDA(cudaEventCreateWithFlags(&m->ready, cudaEventDisableTiming));
+    DB_CUDA(cudaEventRecord(g_ctx.order_ev, g_ctx.stream));
+    DB_CUDA(cudaStreamWaitEvent(g_ctx.xfer, g_ctx.order_ev, 0));
+    DB_CUDA(cudaMemcpyAsync(m->d_data, data, sizeof(double) * n, cudaMemcpyHostToDevice, g_ctx.xfer));
+    DB_CUDA(cudaEventRecord(m->ready, g_ctx.xfer));
+    m->pending = true;
+    return DBCSR_OK;
+}
+
 void free_index(dbcsr_matrix_s* m) {
+    await_data(m);   // a pending upload finishes before its target is freed
     dfree(m->d_rowptr, (size_t)m->nbr + 1);
     dfree(m->d_col, (size_t)(m->nblks ? m->nblks : 1));
     dfree(m->d_row_of, (size_t)(m->nblks ? m->nblks : 1));
@@ -233,6 +267,7 @@ void destroy(dbcsr_matrix_s* m) {
     dfree(m->d_cs, (size_t)m->nbc + 1);
     dfree(m->d_roff, (size_t)m->nbr + 1);
     dfree(m->d_coff, (size_t)m->nbc + 1);
+    if (m->ready) cudaEventDestroy(m->ready);
     delete m;
 }
 
@@ -276,7 +311,10 @@ int dbcsr_set_allocator(dbcsr_alloc_fn alloc, dbcsr_free_fn free_fn, void* actx)
     return DBCSR_OK;
 }
 
-int dbcsr_sync(void) { return sync_stream(); }
+int dbcsr_sync(void) {
+    if (g_ctx.xfer) DB_CUDA(cudaStreamSynchronize(g_ctx.xfer));
+    return sync_stream();
+}
 
 int dbcsr_create(dbcsr_matrix* out, int nbr, int nbc, const int* rs, const int* cs, int64_t nblks,
                  const int* br, const int* bc, const double* data, int data_on_device) {
@@ -353,9 +391,11 @@ int dbcsr_create(dbcsr_matrix* out, int nbr, int nbc, const int* rs, const int* 
             cudaError_t e = cudaMemsetAsync(d_data, 0, sizeof(double) * nelems, g_ctx.stream);
             if (e != cudaSuccess) { destroy(m); return fail(DBCSR_ERR_CUDA, cudaGetErrorString(e)); }
         }
+    } else if (sorted && !data_on_device) {
+        // host values on the transfer stream: the call returns while they copy
+        if ((rc = upload_data(m, data, nelems))) { destroy(m); return rc; }
     } else if (sorted) {
-        cudaError_t e = cudaMemcpyAsync(d_data, data, sizeof(double) * nelems,
-                                        data_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+        cudaError_t e = cudaMemcpyAsync(d_data, data, sizeof(double) * nelems, cudaMemcpyDeviceToDevice,
                                         g_ctx.stream);
         if (e != cudaSuccess) { destroy(m); return fail(DBCSR_ERR_CUDA, cudaGetErrorString(e)); }
     } else {
@@ -425,6 +465,7 @@ int dbcsr_get_index(dbcsr_matrix m, int* br, int* bc, int64_t* off) {
 int dbcsr_get_data(dbcsr_matrix m, double* out, int out_on_device) {
     if (!m || (!out && m->nelems)) return fail(DBCSR_ERR_ARG, "get_data: NULL argument");
     if (m->nelems == 0) return DBCSR_OK;
+    DB_TRY(await_data(m));
     DB_CUDA(cudaMemcpyAsync(out, m->d_data, sizeof(double) * m->nelems,
                             out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, g_ctx.stream));
     if (!out_on_device) DB_TRY(sync_stream());
@@ -434,14 +475,19 @@ int dbcsr_get_data(dbcsr_matrix m, double* out, int out_on_device) {
 int dbcsr_set_data(dbcsr_matrix m, const double* data, int data_on_device) {
     if (!m || (!data && m->nelems)) return fail(DBCSR_ERR_ARG, "set_data: NULL argument");
     if (m->nelems == 0) return DBCSR_OK;
-    DB_CUDA(cudaMemcpyAsync(m->d_data, data, sizeof(double) * m->nelems,
-                            data_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, g_ctx.stream));
+    if (!data_on_device) return upload_data(m, data, m->nelems);
+    DB_TRY(await_data(m));
+    DB_CUDA(cudaMemcpyAsync(m->d_data, data, sizeof(double) * m->nelems, cudaMemcpyDeviceToDevice, g_ctx.stream));
     DB_TRY(sync_stream());
     return DBCSR_OK;
 }
 
 int dbcsr_data_ptr(dbcsr_matrix m, double** p) {
     if (!m || !p) return fail(DBCSR_ERR_ARG, "data_ptr: NULL argument");
+    if (m->pending) {   // the caller may read the values on any stream: the upload completes first
+        DB_CUDA(cudaEventSynchronize(m->ready));
+        m->pending = false;
+    }
     *p = m->d_data;
     return DBCSR_OK;
 }
@@ -458,6 +504,7 @@ int dbcsr_get_block(dbcsr_matrix m, int row, int col, double* out, int* found) {
     if (it == e || *it != col) return DBCSR_OK;
     int64_t q = it - m->h_col.data();
     if (!out) return fail(DBCSR_ERR_ARG, "get_block: out is NULL");
+    DB_TRY(await_data(m));
     DB_TRY(d2h(out, m->d_data + m->h_off[q], sizeof(double) * (m->h_off[q + 1] - m->h_off[q])));
     DB_TRY(sync_stream());
     *found = 1;
@@ -947,6 +994,9 @@ int multiply_dense(bool ta, bool tb, double alpha, dbcsr_matrix_s* A, dbcsr_matr
         g_stats.c_blocks = C->nblks;
         return DBCSR_OK;
     }
+    DB_TRY(await_data(A));
+    DB_TRY(await_data(B));
+    DB_TRY(await_data(C));
     // result pattern: full when both operands are full (and K > 0); else the
     // symbolic product (through stack generation's pattern pass)
     DBuf<double> dA, dB, dC;
@@ -1045,6 +1095,14 @@ extern "C" int dbcsr_multiply(char transa, char transb, double alpha, dbcsr_matr
         return fail(DBCSR_ERR_ARG, "multiply: FP32 runs on the stack path (the dense path offers TF32)");
     g_stats.path = path;
     g_stats.precision = o.precision;
+    // uploads still in flight: the emulated dense path waits for each operand
+    // where it first reads it (the copies of B and C then overlap the work on
+    // A); every other path waits here
+    if (!(path == DBCSR_PATH_DENSE && o.precision == DBCSR_PREC_OZAKI)) {
+        DB_TRY(await_data(A));
+        DB_TRY(await_data(B));
+        DB_TRY(await_data(C));
+    }
     PhaseTimer timer;
     timer.init(o.timing != 0);
     g_timer = timer.on ? &timer : nullptr;

@@ -374,10 +374,11 @@ int oz_exponents(int64_t M, int64_t N, int64_t K, const double* A, int64_t lda, 
     return DBCSR_OK;
 }
 
-// the slice GEMMs and the recombination into `out` (steps 3 and 4)
+// the slice GEMMs and the recombination into `out` (steps 3 and 4); the
+// recombination, the first access to `out`, waits for out_ready when given
 int oz_run(int64_t M, int64_t N, int64_t K, int64_t ldk, int s, const __nv_bfloat16* SA_p,
            const __nv_bfloat16* SB_p, const int* e_p, const int* f_p, double alpha, double beta, const OzOut& out,
-           double* main_flops, int kernel);
+           double* main_flops, int kernel, cudaEvent_t out_ready = nullptr);
 
 int dgemm_ozaki(int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda, const double* B,
                 int64_t ldb, double beta, double* C, int64_t ldc, int s, double* main_flops, int kernel) {
@@ -413,7 +414,7 @@ int dgemm_ozaki(int64_t M, int64_t N, int64_t K, double alpha, const double* A, 
 
 int oz_run(int64_t M, int64_t N, int64_t K, int64_t ldk, int s, const __nv_bfloat16* SA_p,
            const __nv_bfloat16* SB_p, const int* e_p, const int* f_p, double alpha, double beta, const OzOut& out,
-           double* main_flops, int kernel) {
+           double* main_flops, int kernel, cudaEvent_t out_ready) {
     cudaStream_t st = ctx().stream;
     struct { const __nv_bfloat16* p; } SA{SA_p}, SB{SB_p};
     struct { const int* p; } e{e_p}, f{f_p};
@@ -461,6 +462,7 @@ int oz_run(int64_t M, int64_t N, int64_t K, int64_t ldk, int s, const __nv_bfloa
         dim3 g((unsigned)cdiv(N, 32), (unsigned)cdiv(M, 32));
         if (g.y > 65535) return fail(DBCSR_ERR_OVERFLOW, "emulated gemm: M too large for the recombination grid");
         if (p.ksegs >= 512) return fail(DBCSR_ERR_OVERFLOW, "emulated gemm: K too large for exact level sums");
+        if (out_ready) DB_CUDA(cudaStreamWaitEvent(st, out_ready, 0));
         switch (s) {
 #define DB_RC(S_) case S_: k_recombine_rm<S_><<<g, 256, 0, st>>>(M, N, p.ksegs, wsi.p, p.ldws, e.p, f.p, alpha, beta, out); break
             DB_RC(1); DB_RC(2); DB_RC(3); DB_RC(4); DB_RC(5); DB_RC(6); DB_RC(7);
@@ -477,6 +479,7 @@ int oz_run(int64_t M, int64_t N, int64_t K, int64_t ldk, int s, const __nv_bfloa
         DB_TRY(oz_gemm_launch(tmA, tmB, p));
         timer_kernel_end();
         DB_CUDA(cudaMemcpyAsync(&h_err, p.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        if (out_ready) DB_CUDA(cudaStreamWaitEvent(st, out_ready, 0));
         k_recombine<<<(unsigned)cdiv(M * N, 256), 256, 0, st>>>(M, N, s, p.ksegs, ws.p, p.ws_stride, e.p, f.p,
                                                                alpha, beta, C, ldc);
         DB_KCHECK();
@@ -499,7 +502,12 @@ int dgemm_ozaki_blocks(dbcsr_matrix_s* A, bool ta, dbcsr_matrix_s* B, bool tb, d
     if (M >= INT32_MAX || N >= INT32_MAX) return fail(DBCSR_ERR_OVERFLOW, "emulated gemm: dimension too large");
     const int64_t ldk = cdiv(K, 64) * 64;
     DBuf<int> e, f;
+    // operands still uploading: each is awaited where it is first read, so the
+    // later uploads overlap the work on the earlier operands (C's overlaps the
+    // slice GEMMs; the recombination waits for it)
+    DB_TRY(await_data(A));
     DB_TRY(line_exponents(A, !ta, M, e));
+    DB_TRY(await_data(B));
     DB_TRY(line_exponents(B, tb, N, f));
     DBuf<__nv_bfloat16> SA, SB;
     DB_TRY(SA.alloc((size_t)s * M * ldk));
@@ -538,8 +546,12 @@ int dgemm_ozaki_blocks(dbcsr_matrix_s* A, bool ta, dbcsr_matrix_s* B, bool tb, d
     DB_TRY(stride.alloc(M));
     k_full_rows<<<C->nbr, 128, 0, st>>>(C->nbr, C->d_rs, C->d_roff, N, base.p, stride.p);
     DB_KCHECK();
-    return oz_run(M, N, K, ldk, s, SA.p, SB.p, e.p, f.p, alpha, beta, OzOut{C->d_data, 0, base.p, stride.p},
-                  main_flops, kernel);
+    // oz_run orders the recombination, C's first access, after C's upload; on
+    // failure C stays pending and its next use waits again
+    DB_TRY(oz_run(M, N, K, ldk, s, SA.p, SB.p, e.p, f.p, alpha, beta, OzOut{C->d_data, 0, base.p, stride.p},
+                  main_flops, kernel, C->pending ? C->ready : nullptr));
+    C->pending = false;
+    return DBCSR_OK;
 }
 
 int dgemm_emulated(int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda, const double* B,

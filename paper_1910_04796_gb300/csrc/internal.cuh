@@ -63,6 +63,11 @@ struct Context {
     int64_t* d_counters = nullptr;
     // limit of each bounded wait in the tensor-core pipelines (dbcsr_set_wait_limit)
     uint64_t wait_ns = 4000000000ull;
+    // uploads of matrix values from host memory run on their own stream, so
+    // that they overlap the library stream's work (Sec. II: host-to-device
+    // transfers double-buffered against computation with CUDA streams)
+    cudaStream_t xfer = nullptr;
+    cudaEvent_t order_ev = nullptr;   // library-stream point the next upload starts after
 };
 Context& ctx();
 int ensure_device();
@@ -143,6 +148,10 @@ struct dbcsr_matrix_s {
     uint64_t version = 0;    // bumped whenever the pattern changes
     uint64_t uid = 0;
     void* plan = nullptr;    // reusable stack plan + CUDA graph (api.cu)
+    // an upload of the values on the transfer stream that the library stream
+    // has not been ordered after yet; `ready` is recorded when it completes
+    cudaEvent_t ready = nullptr;
+    bool pending = false;
 };
 
 namespace dbcsr {
@@ -169,6 +178,9 @@ OpView make_view(dbcsr_matrix_s* m, bool trans);
 
 int download_index(dbcsr_matrix_s* m);
 void free_index(dbcsr_matrix_s* m);  // index + data + caches, not sizes
+// Order the library stream after a pending upload of m's values (no-op
+// otherwise); every use of m->d_data on the library stream comes after it.
+int await_data(dbcsr_matrix_s* m);
 
 // ------------------------------------------------------------ primitives
 // exclusive scan of n int64 values (in may alias out); total to *d_total (device, may be null)
