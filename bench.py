@@ -115,8 +115,13 @@ def workload(name, scale, occ=0.1):
 
 
 class Clocks:
-    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
-    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+    """nvidia-smi sampling of SM clocks, board power and throttle reasons.
+
+    Each sample carries nvidia-smi's own timestamp; ``window(t0, t1)`` (host
+    time.time() values) restricts the summary to the samples taken inside the
+    timed region. Sampling starts before the warm-up, so that the region is
+    covered from its first step."""
+    Q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
@@ -124,6 +129,7 @@ class Clocks:
         self.index = index
         self.proc = None
         self.lines = []
+        self.t0 = self.t1 = None
 
     def __enter__(self):
         try:
@@ -148,23 +154,38 @@ class Clocks:
             except Exception:
                 self.proc.kill()
 
+    def window(self, t0, t1):
+        self.t0, self.t1 = t0, t1
+
+    @staticmethod
+    def _when(stamp):
+        import datetime
+        try:
+            return datetime.datetime.strptime(stamp, "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
+
     def summary(self):
         sm, mx, pw, reasons = [], [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
-            if len(f) < 7:
+            if len(f) < 8:
                 continue
+            if self.t0 is not None:
+                w = self._when(f[0])
+                if w is None or w < self.t0 or w > self.t1:
+                    continue
             try:
-                sm.append(float(f[0]))
-                mx.append(float(f[1]))
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
             except ValueError:
                 continue
             try:
-                pw.append(float(f[2]))
+                pw.append(float(f[3]))
             except ValueError:
                 pass
-            for n, v in zip(names, f[3:7]):
+            for n, v in zip(names, f[4:8]):
                 if v.lower() == "active":
                     reasons.add(n)
         if not sm:
@@ -265,7 +286,9 @@ def run_reference(args, world, rank):
     return 0
 
 
-def time_steps(fn, steps, warmup, world):
+def time_steps(fn, steps, warmup, world, region=False):
+    """Seconds of `steps` calls of fn on the device (CUDA events), and of wall
+    time; with region=True also the host time.time() bounds of the timed steps."""
     import torch
     for _ in range(warmup):
         fn()
@@ -273,6 +296,7 @@ def time_steps(fn, steps, warmup, world):
     barrier(world)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    h0 = time.time()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record()
@@ -280,15 +304,18 @@ def time_steps(fn, steps, warmup, world):
         fn()
     e1.record()
     torch.cuda.synchronize()
+    h1 = time.time()
     barrier(world)
     wall = time.perf_counter() - t0
+    if region:
+        return e0.elapsed_time(e1) / 1000.0, wall, (h0, h1)
     return e0.elapsed_time(e1) / 1000.0, wall
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="dense-limit")
@@ -346,7 +373,9 @@ def main():
     st = dbcsr.stats()
     useful = st["useful_flops"]
     with Clocks(local) as clk:
-        secs, wall = time_steps(step, args.steps, max(args.warmup, 3) - 1, world)
+        time.sleep(0.5)   # the sampler's first lines come after its start-up
+        secs, wall, region = time_steps(step, args.steps, max(args.warmup, 3) - 1, world, region=True)
+        clk.window(*region)
     launches = dbcsr.stats()["kernel_launches"] * args.steps
     secs = max_over_ranks(secs, world)
     value = aggregate_value(useful, world, args.steps, secs)

@@ -265,23 +265,23 @@ __global__ void __launch_bounds__(256, Q <= 16 ? 2 : 1) k_smm_fp32(SmmArgs g, co
     smm_body<float, Q, TA, TB, 1>(g, g.A32, g.B32, list, nlist, chunk, nullptr, g.counter);
 }
 
-// FP32 stack kernel for blocks up to 32 x 32: a warp per C block; each
-// product's op(A) and op(B) blocks are staged in the warp's shared memory
-// (A(i, l) at l * SA + i, B(l, j) at l * SB + j, with SA and SB the block's
-// padded row and column counts (8, 16 or 32) plus 4: rows 16-byte aligned),
-// and each lane computes an R x CC patch of the C block held in registers: per
-// inner index l it loads R values of A's column l and CC values of B's row l
-// (vector loads) and issues R * CC FMAs. The patch shape follows the padded
-// size, so that all 32 lanes carry work: 8 x 4 patches for 32 x 32 blocks (32
-// FMAs per three vector loads), down to 2 x 1 for 8 x 8. FMA order per
-// element: products in plan order, l ascending. The warp's staging space holds
-// NS stages of the padded size (2 for 32 x 32 blocks, up to 6 for 8 x 8): the
-// asynchronous copies (cp.async, 4 bytes each) of the next NS - 1 products run
-// while the current one is computed. The products' operand offsets and inner
-// sizes are read 32 at a time, one product per lane, and passed on by warp
-// shuffles, so no dependent global load sits between two products. Patch rows
-// from m and columns from n read whatever the staging buffer holds there and
-// feed accumulators that are never stored.
+// FP32 stack kernel for blocks up to 32 x 32. A warp takes a chunk of up to
+// 32 consecutive C blocks of the (class-sorted) order; lane q loads C block
+// q's metadata (sizes, product range, C offsets), so the chunk pays one chain
+// of dependent global loads instead of one per C block. The chunk is split into
+// runs of one patch class, and each run is a single stream of products: the
+// warp stages products NS - 1 ahead across C-block boundaries, computes them
+// in order and writes each C block when its last product is done. Staging:
+// op(A) and op(B) blocks go to the warp's shared memory (A(i, l) at l * SA + i,
+// B(l, j) at l * SB + j, SA and SB the padded row and column counts (8, 16 or
+// 32) plus 4: rows 16-byte aligned; cp.async, 4 bytes each, see f32_stage).
+// Compute: each lane an R x CC patch of the C block in registers; per inner
+// index l it loads R values of A's column l and CC values of B's row l (vector
+// loads) and issues R * CC FMAs. FMA order per element: products in plan
+// order, l ascending. The products' operand offsets and inner sizes are read 32
+// stream positions at a time, one per lane. Patch rows from m and columns from
+// n read whatever the staging buffer holds there and feed accumulators that are
+// never stored.
 constexpr int F32_WARPS = 4;
 constexpr int F32_WARP_FLOATS = 2 * 2 * 32 * 36;   // two stages of 32 x 32 blocks (A and B, rows of 36)
 constexpr int F32_SMEM = F32_WARPS * F32_WARP_FLOATS * (int)sizeof(float);
@@ -294,26 +294,48 @@ __device__ __forceinline__ void cp_async4(float* dst, const float* src) {
 }
 
 // the copies of one product's op(A) (m x kk) and op(B) (kk x n) blocks into a
-// staging buffer (row strides SA, SB); the lane runs along the contiguous index
-// of each stored block
+// staging buffer (row strides SA, SB). Where a stored block's contiguous
+// dimension has at least 16 elements, lane x copies line x of it (one copy per
+// element of the other dimension); below that, lane e copies elements e,
+// e + 32, ... of the block, so that most lanes work on small blocks too. In the
+// second form an element's row and column come from e / d, computed as
+// (e + 1/2) * (1/d) in single precision and truncated: for e < 2^10 and d <= 32
+// the quotient stays at least 1/(2d) away from an integer, far beyond the
+// rounding error, so it truncates to the exact integer quotient.
 template <int TA, int TB, int SA, int SB>
 __device__ __forceinline__ void f32_stage(const float* ga, const float* gb, int m, int n, int kk, float* a_s,
                                           float* b_s, int lane) {
     // op(A): element (i, l) of the stored block at i + l*m (TA = 0) or l + i*kk (TA = 1)
-    if (!TA) {
-        if (lane < m)
-            for (int l = 0; l < kk; l++) cp_async4(a_s + l * SA + lane, ga + lane + l * m);
+    const int da = TA ? kk : m, oa = TA ? m : kk;   // contiguous and other dimension
+    if (da >= 16) {
+        if (lane < da)
+            for (int t = 0; t < oa; t++) {
+                const int i = TA ? t : lane, l = TA ? lane : t;
+                cp_async4(a_s + l * SA + i, ga + lane + t * da);
+            }
     } else {
-        if (lane < kk)
-            for (int i = 0; i < m; i++) cp_async4(a_s + lane * SA + i, ga + lane + i * kk);
+        const float ia = 1.0f / (float)da;
+        for (int e = lane; e < m * kk; e += 32) {
+            const int q = (int)(((float)e + 0.5f) * ia);
+            const int i = TA ? q : e - q * m, l = TA ? e - q * kk : q;
+            cp_async4(a_s + l * SA + i, ga + e);
+        }
     }
     // op(B): element (l, j) at l + j*kk (TB = 0) or j + l*n (TB = 1)
-    if (!TB) {
-        if (lane < kk)
-            for (int j = 0; j < n; j++) cp_async4(b_s + lane * SB + j, gb + lane + j * kk);
+    const int db = TB ? n : kk, ob = TB ? kk : n;
+    if (db >= 16) {
+        if (lane < db)
+            for (int t = 0; t < ob; t++) {
+                const int l = TB ? t : lane, j = TB ? lane : t;
+                cp_async4(b_s + l * SB + j, gb + lane + t * db);
+            }
     } else {
-        if (lane < n)
-            for (int l = 0; l < kk; l++) cp_async4(b_s + l * SB + lane, gb + lane + l * n);
+        const float ib = 1.0f / (float)db;
+        for (int e = lane; e < kk * n; e += 32) {
+            const int q = (int)(((float)e + 0.5f) * ib);
+            const int l = TB ? q : e - q * kk, j = TB ? e - q * n : q;
+            cp_async4(b_s + l * SB + j, gb + e);
+        }
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
 }
@@ -332,93 +354,147 @@ __device__ __forceinline__ void f32_load(const float* p, float (&v)[X]) {
         for (int x = 0; x < X; x++) v[x] = p[x];
     }
 }
-// one C block (m x n, both at most 32) on one warp with R x CC patches, LC
-// lanes across the columns and 32 / LC down the rows; rows padded to RP and
-// columns to CP in the staging buffers. skk: the warp's inner size per stage.
+// one lane's C block of the warp's chunk (lanes past the chunk hold zeros)
+struct F32Blk {
+    int64_t p0 = 0;        // first product
+    int64_t c_off = 0;     // offset of the C block in the new C
+    int64_t cold = -1;     // offset of its old block (beta != 0), -1 none
+    int m = 0, n = 0, cnt = 0;
+};
+
+// A run of nrun C blocks of one patch class (lanes r0 .. r0 + nrun - 1 of the
+// chunk) on one warp, R x CC patches with LC lanes across the columns and
+// 32 / LC down the rows; rows padded to RP and columns to CP in the staging
+// buffers. skk: the warp's inner size per stage.
 template <int TA, int TB, int R, int CC, int LC, int RP, int CP>
-__device__ __forceinline__ void f32_cblock(const SmmArgs& g, int64_t cb, int m, int n, float* wbuf, int* skk,
-                                           int lane, const BlasUpd& bu) {
+__device__ __forceinline__ void f32_run(const SmmArgs& g, const F32Blk& me, int r0, int nrun, float* wbuf,
+                                        int* skk, int lane, const BlasUpd& bu) {
     constexpr int SA = RP + 4, SB = CP + 4;
     constexpr int STAGE = 32 * (SA + SB);
     constexpr int NS = F32_WARP_FLOATS / STAGE < F32_MAX_STAGES ? F32_WARP_FLOATS / STAGE : F32_MAX_STAGES;
     static_assert(NS >= 2, "two stages at least");
+    const unsigned full = 0xffffffffu;
     const int row0 = (lane / LC) * R, col0 = (lane % LC) * CC;
-    const int64_t p0 = g.c_pstart[cb], p1 = g.c_pstart[cb + 1];
-    float acc[R][CC];
+    // the run's product stream: C block i covers positions [excl_i, incl_i)
+    const bool in_run = lane >= r0 && lane < r0 + nrun;
+    int64_t incl = in_run ? me.cnt : 0;
 #pragma unroll
-    for (int r = 0; r < R; r++)
+    for (int d = 1; d < 32; d <<= 1) {
+        const int64_t v = __shfl_up_sync(full, incl, d);
+        if (lane >= d) incl += v;
+    }
+    const int64_t excl = incl - (in_run ? me.cnt : 0);
+    const int64_t total = __shfl_sync(full, incl, 31);
+    // lane of the C block that holds stream position s (s < total, per lane):
+    // the first lane of the run whose inclusive end exceeds s. A lower-bound
+    // search with a fixed six halvings (enough for 32 lanes), so that every
+    // lane runs every shuffle; only the bounds update is conditional.
+    auto owner_of = [&](int64_t s) {
+        int first = r0, count = nrun;
 #pragma unroll
-        for (int c = 0; c < CC; c++) acc[r][c] = 0.f;
-    // descriptors of products pbase .. pbase + 31, one per lane
-    int64_t pbase = p0 - 32, d_ao = 0, d_bo = 0;
+        for (int it = 0; it < 6; it++) {
+            const int step = count >> 1;
+            const int idx = min(first + step, 31);
+            const int64_t v = __shfl_sync(full, incl, idx);
+            if (count > 0) {
+                if (v <= s) {
+                    first += step + 1;
+                    count -= step + 1;
+                } else {
+                    count = step;
+                }
+            }
+        }
+        return first;
+    };
+    // descriptors of stream positions sbase .. sbase + 31, one per lane
+    int64_t sbase = -32, d_ao = 0, d_bo = 0;
     int d_kk = 0;
-    // stage product p (products are staged once each, in ascending order) into slot s
-    auto stage = [&](int64_t p, int s) {
-        if (p >= pbase + 32) {
-            pbase = p;
-            const int64_t q = p + lane;
-            if (q < p1) {
-                const int2 pr = g.prod[q];
+    auto stage = [&](int64_t s2, int slot) {   // s2 uniform, ascending across calls
+        if (s2 >= sbase + 32) {
+            sbase = s2;
+            const int64_t mine = s2 + lane;
+            // every lane takes part in the searches' shuffles
+            const int ow = owner_of(mine < total ? mine : total - 1);
+            const int64_t p = __shfl_sync(full, me.p0, ow) + (mine - __shfl_sync(full, excl, ow));
+            const int om = __shfl_sync(full, me.m, ow);
+            if (mine < total) {
+                const int2 pr = g.prod[p];
                 d_ao = g.A.off[pr.x];
-                d_kk = (int)((g.A.off[pr.x + 1] - d_ao) / m);
+                d_kk = (int)((g.A.off[pr.x + 1] - d_ao) / om);
                 d_bo = g.B.off[pr.y];
             }
         }
-        const int src = (int)(p - pbase);
-        const int64_t ao = __shfl_sync(0xffffffffu, d_ao, src);
-        const int64_t bo = __shfl_sync(0xffffffffu, d_bo, src);
-        const int kk = __shfl_sync(0xffffffffu, d_kk, src);
-        if (lane == 0) skk[s] = kk;
-        float* a_s = wbuf + s * STAGE;
+        const int src = (int)(s2 - sbase);
+        const int64_t ao = __shfl_sync(full, d_ao, src);
+        const int64_t bo = __shfl_sync(full, d_bo, src);
+        const int kk = __shfl_sync(full, d_kk, src);
+        const unsigned before = __ballot_sync(full, in_run && incl <= s2);
+        const int ow = r0 + __popc(before);
+        const int m = __shfl_sync(full, me.m, ow), n = __shfl_sync(full, me.n, ow);
+        if (lane == 0) skk[slot] = kk;
+        float* a_s = wbuf + slot * STAGE;
         f32_stage<TA, TB, SA, SB>(g.A32 + ao, g.B32 + bo, m, n, kk, a_s, a_s + 32 * SA, lane);
     };
 #pragma unroll 1
-    for (int s = 0; s < NS - 1; s++) {
-        if (p0 + s < p1) stage(p0 + s, s);
+    for (int t = 0; t < NS - 1; t++) {
+        if (t < total) stage(t, t);
         else asm volatile("cp.async.commit_group;" ::: "memory");
     }
-    int cs = 0;   // slot of product p
+    int64_t s = 0;   // stream position being computed
+    int cs = 0;      // its slot
 #pragma unroll 1
-    for (int64_t p = p0; p < p1; p++) {
-        // slot cs - 1 (mod NS) was last read by product p - 1, finished by every lane
-        __syncwarp();
-        if (p + NS - 1 < p1) stage(p + NS - 1, cs == 0 ? NS - 1 : cs - 1);
-        else asm volatile("cp.async.commit_group;" ::: "memory");
-        asm volatile("cp.async.wait_group %0;" ::"n"(NS - 1) : "memory");
-        __syncwarp();   // product p's blocks are in shared memory for every lane
-        const int cur_kk = skk[cs];
-        const float* ar = wbuf + cs * STAGE + row0;
-        const float* bc = wbuf + cs * STAGE + 32 * SA + col0;
+    for (int i = 0; i < nrun; i++) {
+        const int li = r0 + i;
+        const int cnt = __shfl_sync(full, me.cnt, li);
+        float acc[R][CC];
+#pragma unroll
+        for (int r = 0; r < R; r++)
+#pragma unroll
+            for (int c = 0; c < CC; c++) acc[r][c] = 0.f;
+#pragma unroll 1
+        for (int c = 0; c < cnt; c++, s++) {
+            // slot cs - 1 (mod NS) was last read by position s - 1, finished by every lane
+            __syncwarp();
+            if (s + NS - 1 < total) stage(s + NS - 1, cs == 0 ? NS - 1 : cs - 1);
+            else asm volatile("cp.async.commit_group;" ::: "memory");
+            asm volatile("cp.async.wait_group %0;" ::"n"(NS - 1) : "memory");
+            __syncwarp();   // position s's blocks are in shared memory for every lane
+            const int cur_kk = skk[cs];
+            const float* ar = wbuf + cs * STAGE + row0;
+            const float* bc = wbuf + cs * STAGE + 32 * SA + col0;
 #pragma unroll 2
-        for (int l = 0; l < cur_kk; l++) {
-            float av[R], bv[CC];
-            f32_load<R>(ar + l * SA, av);
-            f32_load<CC>(bc + l * SB, bv);
+            for (int l = 0; l < cur_kk; l++) {
+                float av[R], bv[CC];
+                f32_load<R>(ar + l * SA, av);
+                f32_load<CC>(bc + l * SB, bv);
 #pragma unroll
-            for (int r = 0; r < R; r++)
+                for (int r = 0; r < R; r++)
 #pragma unroll
-                for (int c = 0; c < CC; c++) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
+                    for (int q = 0; q < CC; q++) acc[r][q] = fmaf(av[r], bv[q], acc[r][q]);
+            }
+            cs = cs + 1 == NS ? 0 : cs + 1;
         }
-        cs = cs + 1 == NS ? 0 : cs + 1;
-    }
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-    __syncwarp();   // the next C block's first copies overwrite the slots
-    // alpha / beta in FP64, column-major C block
-    double* cout = g.Cd + g.c_off[cb];
-    const int o = g.c_old ? g.c_old[cb] : -1;
-    const double* cold = o >= 0 ? g.Cold + g.Cold_off[o] : nullptr;
+        // alpha / beta in FP64, column-major C block
+        const int m = __shfl_sync(full, me.m, li), n = __shfl_sync(full, me.n, li);
+        double* cout = g.Cd + __shfl_sync(full, me.c_off, li);
+        const int64_t co = __shfl_sync(full, me.cold, li);
+        const double* cold = co >= 0 ? g.Cold + co : nullptr;
 #pragma unroll
-    for (int c = 0; c < CC; c++) {
-        const int j = col0 + c;
+        for (int c = 0; c < CC; c++) {
+            const int j = col0 + c;
 #pragma unroll
-        for (int r = 0; r < R; r++) {
-            const int i = row0 + r;
-            if (i < m && j < n) {
-                const int64_t e = (int64_t)j * m + i;
-                cout[e] = cold ? bu.update((double)acc[r][c], cold[e]) : bu.scale((double)acc[r][c]);
+            for (int r = 0; r < R; r++) {
+                const int ii = row0 + r;
+                if (ii < m && j < n) {
+                    const int64_t e = (int64_t)j * m + ii;
+                    cout[e] = cold ? bu.update((double)acc[r][c], cold[e]) : bu.scale((double)acc[r][c]);
+                }
             }
         }
     }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncwarp();   // the next run's first copies overwrite the slots
 }
 
 __device__ __forceinline__ int f32_class(int x) { return x <= 8 ? 0 : (x <= 16 ? 1 : 2); }
@@ -438,36 +514,51 @@ __global__ void k_f32_classify(int64_t nC, const int* __restrict__ c_row, const 
 
 template <int TA, int TB>
 __global__ void __launch_bounds__(32 * F32_WARPS, 3) k_smm_f32_tile(SmmArgs g, const uint32_t* __restrict__ order,
-                                                                 int chunk) {
+                                                                    int chunk) {
     extern __shared__ __align__(16) float f32_smem[];
-    __shared__ int s_cb[F32_WARPS];
     __shared__ int s_kk[F32_WARPS][F32_MAX_STAGES];
+    const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float* wbuf = f32_smem + warp * F32_WARP_FLOATS;
     int* skk = s_kk[warp];
     const BlasUpd bu(g.alpha, g.beta);
     for (;;) {
-        if (lane == 0) s_cb[warp] = (int)atomicAdd(g.counter, (unsigned long long)chunk);
-        __syncwarp();
-        const int64_t base = s_cb[warp];
-        __syncwarp();
+        unsigned long long b = 0;
+        if (lane == 0) b = atomicAdd(g.counter, (unsigned long long)chunk);
+        const int64_t base = (int64_t)__shfl_sync(full, b, 0);
         if (base >= g.nC) break;
-        const int64_t cend = min(base + (int64_t)chunk, g.nC);
-        for (int64_t q = base; q < cend; q++) {
-            const int64_t cb = order ? (int64_t)order[q] : q;
-            const int m = g.rsC[g.c_row[cb]], n = g.csC[g.c_col[cb]];
-            // patch shape by padded size (rows 8 / 16 / 32) x (columns 8 / 16 / 32)
-            switch (f32_class(m) * 3 + f32_class(n)) {
-                case 0: f32_cblock<TA, TB, 2, 1, 8, 8, 8>(g, cb, m, n, wbuf, skk, lane, bu); break;
-                case 1: f32_cblock<TA, TB, 2, 2, 8, 8, 16>(g, cb, m, n, wbuf, skk, lane, bu); break;
-                case 2: f32_cblock<TA, TB, 2, 4, 8, 8, 32>(g, cb, m, n, wbuf, skk, lane, bu); break;
-                case 3: f32_cblock<TA, TB, 2, 2, 4, 16, 8>(g, cb, m, n, wbuf, skk, lane, bu); break;
-                case 4: f32_cblock<TA, TB, 4, 2, 8, 16, 16>(g, cb, m, n, wbuf, skk, lane, bu); break;
-                case 5: f32_cblock<TA, TB, 4, 4, 8, 16, 32>(g, cb, m, n, wbuf, skk, lane, bu); break;
-                case 6: f32_cblock<TA, TB, 4, 2, 4, 32, 8>(g, cb, m, n, wbuf, skk, lane, bu); break;
-                case 7: f32_cblock<TA, TB, 4, 4, 4, 32, 16>(g, cb, m, n, wbuf, skk, lane, bu); break;
-                default: f32_cblock<TA, TB, 8, 4, 8, 32, 32>(g, cb, m, n, wbuf, skk, lane, bu); break;
+        const int cnt = (int)min((int64_t)chunk, g.nC - base);   // chunk <= 32
+        // lane q: C block q of the chunk
+        F32Blk me;
+        int cls = -1;
+        if (lane < cnt) {
+            const int64_t cb = order ? (int64_t)order[base + lane] : base + lane;
+            me.m = g.rsC[g.c_row[cb]];
+            me.n = g.csC[g.c_col[cb]];
+            me.p0 = g.c_pstart[cb];
+            me.cnt = (int)(g.c_pstart[cb + 1] - me.p0);
+            me.c_off = g.c_off[cb];
+            const int o = g.c_old ? g.c_old[cb] : -1;
+            me.cold = o >= 0 ? g.Cold_off[o] : -1;
+            cls = f32_class(me.m) * 3 + f32_class(me.n);
+        }
+        // runs of one patch class
+        for (int r0 = 0; r0 < cnt;) {
+            const int c0 = __shfl_sync(full, cls, r0);
+            const unsigned other = __ballot_sync(full, lane > r0 && lane < cnt && cls != c0);
+            const int r1 = other ? __ffs(other) - 1 : cnt;
+            switch (c0) {   // patch shape by padded size (rows 8 / 16 / 32) x (columns 8 / 16 / 32)
+                case 0: f32_run<TA, TB, 2, 1, 8, 8, 8>(g, me, r0, r1 - r0, wbuf, skk, lane, bu); break;
+                case 1: f32_run<TA, TB, 2, 2, 8, 8, 16>(g, me, r0, r1 - r0, wbuf, skk, lane, bu); break;
+                case 2: f32_run<TA, TB, 2, 4, 8, 8, 32>(g, me, r0, r1 - r0, wbuf, skk, lane, bu); break;
+                case 3: f32_run<TA, TB, 2, 2, 4, 16, 8>(g, me, r0, r1 - r0, wbuf, skk, lane, bu); break;
+                case 4: f32_run<TA, TB, 4, 2, 8, 16, 16>(g, me, r0, r1 - r0, wbuf, skk, lane, bu); break;
+                case 5: f32_run<TA, TB, 4, 4, 8, 16, 32>(g, me, r0, r1 - r0, wbuf, skk, lane, bu); break;
+                case 6: f32_run<TA, TB, 4, 2, 4, 32, 8>(g, me, r0, r1 - r0, wbuf, skk, lane, bu); break;
+                case 7: f32_run<TA, TB, 4, 4, 4, 32, 16>(g, me, r0, r1 - r0, wbuf, skk, lane, bu); break;
+                default: f32_run<TA, TB, 8, 4, 8, 32, 32>(g, me, r0, r1 - r0, wbuf, skk, lane, bu); break;
             }
+            r0 = r1;
         }
     }
 }
@@ -757,7 +848,8 @@ int smm_fp32_dispatch(const SmmArgs& g, int max_mn, int max_edge) {
         DB_TRY(radix_sort_u32(key.p, order.p, g.nC, 4));
         int grid = ctx().num_sms * 3;
         if ((int64_t)grid * F32_WARPS > g.nC) grid = (int)cdiv(g.nC, F32_WARPS);
-        const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(16, g.nC / ((int64_t)grid * F32_WARPS * 4)));
+        // C blocks per grab: up to 32 (one per lane), at least ~4 grabs per warp
+        const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(32, g.nC / ((int64_t)grid * F32_WARPS * 4)));
         const int ta = g.A.trans, tb = g.B.trans;
 #define DB_LAUNCH_F32(TA_, TB_)                                                                          \
     do {                                                                                                \

@@ -89,17 +89,24 @@ def test_committed_traffic_rows_name_existing_sources():
 def test_clock_summary():
     c = bench.Clocks()
     c.lines = [
-        "1965, 2070, 1180.2, Not Active, Not Active, Not Active, Active",
-        "1890, 2070, 1201.0, Not Active, Not Active, Not Active, Active",
-        "2010, 2070, 1150.7, Not Active, Not Active, Not Active, Not Active",
+        "2026/12/04 10:00:00.100, 1965, 2070, 1180.2, Not Active, Not Active, Not Active, Active",
+        "2026/12/04 10:00:00.200, 1890, 2070, 1201.0, Not Active, Not Active, Not Active, Active",
+        "2026/12/04 10:00:00.300, 2010, 2070, 1150.7, Not Active, Not Active, Not Active, Not Active",
         "garbage line",
-        "[N/A], 2070, 1, Not Active, Not Active, Not Active, Not Active",
+        "2026/12/04 10:00:00.400, [N/A], 2070, 1, Not Active, Not Active, Not Active, Not Active",
     ]
     s = c.summary()
     assert s == {"sm_mhz": 1965.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3,
                  "power_w": 1180.2}
-    c.lines.append("1200, 2070, 900.0, Active, Not Active, Active, Not Active")
+    c.lines.append("2026/12/04 10:00:00.500, 1200, 2070, 900.0, Active, Not Active, Active, Not Active")
     assert c.summary()["reasons"] == ["hw_slowdown", "sw_power_cap", "sw_thermal_slowdown"]
+    # only the samples inside the timed region count
+    t = bench.Clocks._when("2026/12/04 10:00:00.150")
+    c.window(t, t + 0.2)
+    s = c.summary()
+    assert s["samples"] == 2 and s["sm_mhz"] == 1950.0 and s["reasons"] == ["sw_power_cap"]
+    c.window(t + 10, t + 11)
+    assert c.summary()["reasons"] == ["unsampled"]
     empty = bench.Clocks()
     assert empty.summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
 
