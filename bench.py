@@ -331,6 +331,8 @@ def main():
                     help="stack kernel choice passed to dbcsr_multiply (0 = automatic)")
     ap.add_argument("--ref-rows", type=int, default=48, help="C block rows per oracle sample")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-serial", action="store_true",
+                    help="end to end: wait for each upload before the next call (the copies do not overlap)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-legs", action="store_true", help="skip the plain-FP64 comparison legs")
     args = ap.parse_args()
@@ -448,12 +450,17 @@ def main():
         def e2e_step():
             nonlocal out
             t0 = time.perf_counter()
+            # --e2e-serial: every upload finished before the next call (no overlap)
+            wait = dbcsr.sync if args.e2e_serial else (lambda: None)
             Ah = dbcsr.Matrix.create(w.A.row_sizes, w.A.col_sizes, w.A.blk_row, w.A.blk_col, hA)
+            wait()
             Bh = dbcsr.Matrix.create(w.B.row_sizes, w.B.col_sizes, w.B.blk_row, w.B.blk_col, hB)
+            wait()
             if C0 is not None:
                 Ch = dbcsr.Matrix.create(C0.row_sizes, C0.col_sizes, C0.blk_row, C0.blk_col, hC)
             else:
                 Ch = dbcsr.Matrix.create(rs, cs, np.zeros(0, np.int32), np.zeros(0, np.int32))
+            wait()
             t1 = time.perf_counter()
             dbcsr.multiply(w.transa, w.transb, w.alpha, Ah, Bh, w.beta, Ch, path=args.path, precision=precision,
                            ozaki_slices=args.slices, kernel=args.kernel, hybrid_panel=hpanel,
