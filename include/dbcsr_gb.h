@@ -186,8 +186,8 @@ DBCSR_API int dbcsr_set_allocator(dbcsr_alloc_fn alloc, dbcsr_free_fn free_fn, v
  * Host values in CSR order from page-locked (pinned) memory are copied on the
  * library's transfer stream: the call returns while they copy, the matrix's
  * next use waits for the copy, and `data` must stay unchanged until a call
- * that synchronises has returned (dbcsr_sync(), or any call that returns the
- * matrix's values to the host). From pageable memory the copy is complete
+ * that synchronises has returned (dbcsr_sync(), dbcsr_release() of the
+ * matrix, or any call that returns the matrix's values to the host). From pageable memory the copy is complete
  * when the call returns.
  * Blocks are stored in CSR order (row, then column ascending). */
 DBCSR_API int dbcsr_create(dbcsr_matrix *out, int nblkrows, int nblkcols,
@@ -197,7 +197,9 @@ DBCSR_API int dbcsr_create(dbcsr_matrix *out, int nblkrows, int nblkcols,
 
 /* Free a matrix and set *m to NULL. NULL or *m == NULL is a no-op. Its device
  * memory returns to the pool it came from (Sec. III: memory-pool buffers on
- * the GPU reduce the time spent in allocations). */
+ * the GPU reduce the time spent in allocations). A copy of its values from
+ * page-locked host memory still in flight is waited for first, so the
+ * caller may free that memory once this call returns. */
 DBCSR_API int dbcsr_release(dbcsr_matrix *m);
 
 /* Block grid, number of stored blocks and of stored elements of a matrix in

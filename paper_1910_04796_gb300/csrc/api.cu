@@ -261,6 +261,9 @@ void free_plan(dbcsr_matrix_s* m) {
 
 void destroy(dbcsr_matrix_s* m) {
     if (!m) return;
+    // a copy from the caller's page-locked memory still in flight: the caller
+    // may free that memory once the matrix is released
+    if (m->pending) cudaEventSynchronize(m->ready);
     free_plan(m);
     free_index(m);
     dfree(m->d_rs, (size_t)m->nbr + 1);
