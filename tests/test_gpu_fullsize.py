@@ -15,6 +15,10 @@ with the same definition:
   oracle runs on the sampled rows of op(A) against the whole op(B).
 * Reported precisions (emulated against the near-exact Dot2 product, TF32)
   within their gates on the same normalisation.
+* FP32 (stack path): sampled C block rows against the oracle's FP32 product
+  (inputs rounded to FP32, FP32 products and sums), within 2 gamma_K on the
+  same normalisation, K the longest inner product of the sampled rows: each
+  side is within gamma_K |A||B| of the exact product of the rounded inputs.
 """
 import numpy as np
 import pytest
@@ -221,3 +225,24 @@ def test_precision_sparse_1024_emulated_stacks():
     ref = O.multiply("N", "N", 1.0, w.A, w.B, 0.0, rows=rows, mode=1)
     check_block_rows(got, ref, w.A, w.B, 1e-12)
     check_emulated_rows(w, got, sample_rows(32768, 8, seed=15))
+
+
+def fp32_bar(A, rows):
+    """2 gamma_K, K the longest inner product of the given C block rows (u = 2^-24)."""
+    cs = np.asarray(A.col_sizes, np.int64)
+    K = max(int(np.sum(cs[A.blk_col[A.blk_row == r]])) for r in rows)
+    u = 2.0 ** -24
+    return 2 * K * u / (1 - K * u)
+
+
+@pytest.mark.parametrize("name", ["uneven", "precision-sparse"])
+def test_fp32_stacks_full_size(name):
+    # the configuration bench.py times with --precision fp32 --path stacks
+    if name == "uneven":
+        w, rows = synth.workload_uneven(), sample_rows(4000, 24, seed=6)
+    else:
+        w, rows = synth.workload_precision_sparse(), sample_rows(1024, 8, seed=7)
+    got, st = run(w, "stacks", "fp32")
+    assert st["path"] == dbcsr.PATH_STACKS and st["precision"] == dbcsr.PREC_FP32
+    ref = O.multiply("N", "N", 1.0, w.A, w.B, 0.0, rows=rows, mode=2)
+    check_block_rows(got, ref, w.A, w.B, fp32_bar(w.A, rows))
