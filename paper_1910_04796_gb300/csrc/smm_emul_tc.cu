@@ -106,6 +106,14 @@ struct TcGeo {
     static constexpr int SMEM0 = NST * STAGE + LS + RESERVE;
     static constexpr int SMEM = SMEM0 < TC_SMEM_MIN ? TC_SMEM_MIN : SMEM0;
     static constexpr uint32_t IDESC = ptx::idesc_f32acc(1, 128, N);
+    // segments 1 and 2 hold needed pairs only in columns u = 4 .. S - 1 and
+    // u = 5 (pairs (q+4, u-3) and (8, u-4) with t + u' <= S + 1): their MMAs
+    // cover just those columns (N1, N2 at column 32 * 3 and 32 * 4) with B's
+    // window starting at slice 1
+    static constexpr int N1 = S >= 5 ? 32 * (S - 4) : 32;
+    static constexpr int N2 = S >= 8 ? 32 * (S - 7) : 32;
+    static constexpr uint32_t IDESC1 = ptx::idesc_f32acc(1, 128, N1);
+    static constexpr uint32_t IDESC2 = ptx::idesc_f32acc(1, 128, N2);
     static_assert(N <= TC_ACC_COLS, "accumulator exceeds its TMEM buffer");
     static_assert(NSEG * CHUNK * 32 * 127 * 127 < (1 << 24), "fp32 stretch not exact");
     static_assert(NST >= 2, "at least two pipeline stages");
@@ -348,14 +356,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_smm_emul_tc(TcArgs a) {
                         const uint8_t* sb = sa + G::A_SLOTS * TC_SLOT;
 #pragma unroll
                         for (int sg = 0; sg < G::NSEG; sg++) {
-                            const int bslot = sg == 0 ? G::B_ZERO : (sg == 1 ? G::B_ZERO - 3 : G::B_ZERO - 4);
+                            // segment sg >= 1 starts at accumulator column 32 * (sg + 2)
+                            const uint32_t dcol = sg == 0 ? 0u : (uint32_t)(32 * (sg + 2));
+                            const uint32_t idesc = sg == 0 ? G::IDESC : (sg == 1 ? G::IDESC1 : G::IDESC2);
                             const uint64_t ad = ptx::smem_desc_kmajor(sa + 4 * sg * TC_SLOT, 128, 512);
-                            const uint64_t bd = ptx::smem_desc_kmajor(sb + bslot * TC_SLOT, 128, 512);
+                            const uint64_t bd = ptx::smem_desc_kmajor(sb + G::B_ZERO * TC_SLOT, 128, 512);
 #pragma unroll
                             for (int ks = 0; ks < 2; ks++) {
-                                // the second K = 16 step starts two core matrices (256 bytes) further
+                                // the second K = 16 step starts two core matrices (256 bytes) further;
+                                // segment 0 of a chunk's first product initialises every column
                                 const uint32_t acc = (p > c0 || sg > 0 || ks > 0) ? 1u : 0u;
-                                ptx::mma_f16_ss(d, ad + (uint64_t)(ks * 16), bd + (uint64_t)(ks * 16), G::IDESC, acc);
+                                ptx::mma_f16_ss(d + dcol, ad + (uint64_t)(ks * 16), bd + (uint64_t)(ks * 16), idesc,
+                                                acc);
                             }
                         }
                         ptx::mma_commit(&empty[st]);
@@ -499,7 +511,8 @@ int launch_tc(const TcArgs& a, int grid) {
 template <int S>
 double issued_per_product() {
     using G = TcGeo<S>;
-    return 2.0 * 128.0 * (double)G::N * 32.0 * (double)G::NSEG;
+    const double cols = (double)G::N + (G::NSEG > 1 ? (double)G::N1 : 0.0) + (G::NSEG > 2 ? (double)G::N2 : 0.0);
+    return 2.0 * 128.0 * cols * 32.0;
 }
 
 }  // namespace
