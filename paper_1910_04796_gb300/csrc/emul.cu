@@ -141,15 +141,6 @@ __global__ void k_recombine(int64_t M, int64_t N, int s, int ksegs, const double
     C[i + j * ldc] = bu.old ? bu.update(x, C[i + j * ldc]) : bu.scale(x);
 }
 
-// 2^k as a double for -1022 <= k <= 1023 (exact bit pattern)
-__device__ __forceinline__ double pow2(int k) { return __longlong_as_double((long long)(1023 + k) << 52); }
-
-// acc * 2^k rounded once, like ldexp(acc, k): a product by an exact normal
-// power of two is correctly rounded; outside that range ldexp itself is used
-__device__ __forceinline__ double scale2(double acc, int k) {
-    return (k >= -1022 && k <= 1023) ? acc * pow2(k) : ldexp(acc, k);
-}
-
 // Recombination from int32 row-major level sums ws[d-2][kseg][i][j] (row
 // stride ldws) into column-major C, through a 32 x 32 shared-memory tile so
 // that both the reads and the writes are coalesced. Same arithmetic and order

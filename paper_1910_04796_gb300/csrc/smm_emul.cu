@@ -143,7 +143,6 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
                  "l"(src)
                  : "memory");
 }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>

@@ -308,8 +308,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_smm_emul_tc(TcArgs a) {
                     const uint8_t* ga = a.SA + (int64_t)pr.x * (S * TC_SLOT);
                     ptx::mbar_arrive_expect_tx(&full[st], 2 * S * TC_SLOT);
                     ptx::bulk_load(sa, ga, (S < 4 ? S : 4) * TC_SLOT, &full[st]);
-                    if (S > 4) ptx::bulk_load(sa + 5 * TC_SLOT, ga + 4 * TC_SLOT, ((S < 7 ? S : 7) - 4) * TC_SLOT, &full[st]);
-                    if (S > 7) ptx::bulk_load(sa + 11 * TC_SLOT, ga + 7 * TC_SLOT, TC_SLOT, &full[st]);
+                    if constexpr (S > 4)
+                        ptx::bulk_load(sa + 5 * TC_SLOT, ga + 4 * TC_SLOT, ((S < 7 ? S : 7) - 4) * TC_SLOT, &full[st]);
+                    if constexpr (S > 7) ptx::bulk_load(sa + 11 * TC_SLOT, ga + 7 * TC_SLOT, TC_SLOT, &full[st]);
                     ptx::bulk_load(sb + G::B_ZERO * TC_SLOT, a.SB + (int64_t)pr.y * (S * TC_SLOT), S * TC_SLOT,
                                    &full[st]);
                 }
