@@ -470,7 +470,7 @@ def main():
             t3 = time.perf_counter()
             for m in (Ah, Bh, Ch):
                 m.release()
-            phases.append((t1 - t0, t2 - t1, t3 - t2))
+            phases.append((t1 - t0, t2 - t1, t3 - t2, time.perf_counter() - t0))
 
         e2e_steps = max(1, args.steps)
         s_e2e, _ = time_steps(e2e_step, e2e_steps, 2, world)
@@ -483,7 +483,10 @@ def main():
                # median host time of each call group per step: the creates return while
                # page-locked values still copy, so their copies overlap the multiply
                "phases_ms": {k: 1e3 * statistics.median(p[q] for p in timed)
-                             for q, k in enumerate(("creates", "multiply", "read_back"))}}
+                             for q, k in enumerate(("creates", "multiply", "read_back"))},
+               # host time of whole steps: a few slow steps (shared host links) pull the mean down
+               "step_ms": {"median": 1e3 * statistics.median(p[3] for p in timed),
+                           "max": 1e3 * max(p[3] for p in timed)}}
 
     # comparison legs on the same GPU and inputs: the plain FP64 paths, the
     # emulated and TF32 paths with their error against the GPU FP64 result
