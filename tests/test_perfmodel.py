@@ -129,3 +129,20 @@ def test_mnk_table_string_roundtrip():
     m, n, k, v = entries[37]
     assert code[((m - 1) * E + (n - 1)) * E + (k - 1)] == str(v)
     assert autotune.decode_mnk(code, E) == entries
+
+
+def test_shipped_tables_follow_from_their_records():
+    # the GB300 model file keeps the timed training records; refitting the
+    # performance model on them (no GPU) gives the very tables the file ships
+    import json
+    import os
+    from paper_1910_04796_gb300 import autotune
+    with open(autotune.MODEL_TABLE) as f:
+        d = json.load(f)
+    recs = [tuple(r) for r in d["records"]]
+    assert len(recs) == 4 * d["report"]["timed_for_training"]
+    E = int(d["variants_mnk"]["max_edge"])
+    entries, entries_mnk, _, _ = autotune.model_tune(d["report"]["sizes"], d["report"]["train_frac"], 3, E, False,
+                                                     recs=recs)
+    assert [e[:3] for e in entries] == [e[:3] for e in d["entries"]]
+    assert autotune.encode_mnk(entries_mnk, E) == d["variants_mnk"]["variants"]
