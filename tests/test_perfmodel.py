@@ -135,7 +135,6 @@ def test_shipped_tables_follow_from_their_records():
     # the GB300 model file keeps the timed training records; refitting the
     # performance model on them (no GPU) gives the very tables the file ships
     import json
-    import os
     from paper_1910_04796_gb300 import autotune
     with open(autotune.MODEL_TABLE) as f:
         d = json.load(f)
