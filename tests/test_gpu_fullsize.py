@@ -217,6 +217,16 @@ def test_precision_dense_N16384(precision, tol):
     check_block_rows(got, ref, w.A, w.B, tol)
 
 
+def test_precision_sparse_1024_fp64_stacks():
+    # FP64 stack kernels on the 1 024^2 grid of 32 x 32 blocks (two passes of 16 elements per lane)
+    w = synth.workload_precision_sparse()
+    got, st = run(w, "auto", "fp64")
+    assert st["path"] == dbcsr.PATH_STACKS
+    rows = sample_rows(1024, 8, seed=8)
+    ref = O.multiply("N", "N", 1.0, w.A, w.B, 0.0, rows=rows)
+    check_block_rows(got, ref, w.A, w.B, 1e-13)
+
+
 def test_precision_sparse_1024_emulated_stacks():
     w = synth.workload_precision_sparse()
     got, st = run(w, "stacks", "ozaki")
