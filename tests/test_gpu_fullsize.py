@@ -245,14 +245,18 @@ def fp32_bar(A, rows):
     return 2 * K * u / (1 - K * u)
 
 
-@pytest.mark.parametrize("name", ["uneven", "precision-sparse"])
+@pytest.mark.parametrize("name", ["uneven", "precision-sparse", "dense-limit"])
 def test_fp32_stacks_full_size(name):
-    # the configuration bench.py times with --precision fp32 --path stacks
+    # the configuration bench.py times with --precision fp32 --path stacks (the
+    # dense limit with beta = 1: the old-C term is the same FP64 step on both sides)
     if name == "uneven":
         w, rows = synth.workload_uneven(), sample_rows(4000, 24, seed=6)
-    else:
+    elif name == "precision-sparse":
         w, rows = synth.workload_precision_sparse(), sample_rows(1024, 8, seed=7)
+    else:
+        w, rows = synth.workload_dense_limit(), sample_rows(512, 3, seed=9)
     got, st = run(w, "stacks", "fp32")
     assert st["path"] == dbcsr.PATH_STACKS and st["precision"] == dbcsr.PREC_FP32
-    ref = O.multiply("N", "N", 1.0, w.A, w.B, 0.0, rows=rows, mode=2)
+    beta = w.beta if w.C is not None else 0.0
+    ref = O.multiply("N", "N", w.alpha, w.A, w.B, beta, w.C, rows=rows, mode=2)
     check_block_rows(got, ref, w.A, w.B, fp32_bar(w.A, rows))
