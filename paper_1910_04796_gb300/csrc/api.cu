@@ -1000,6 +1000,20 @@ int multiply_dense(bool ta, bool tb, double alpha, dbcsr_matrix_s* A, dbcsr_matr
     DB_TRY(await_data(A));
     DB_TRY(await_data(B));
     DB_TRY(await_data(C));
+    // TF32 with fully occupied operands of one block size per dimension: the
+    // TF32 operands straight from the blocks and the GEMM's result straight
+    // into C's blocks (no dense copies)
+    if (o.precision == DBCSR_PREC_TF32 && a_full && b_full && nbk > 0 && M > 0 && N > 0 && K > 0 &&
+        (!use_old || c_full) && tf32_blocks_ok(A, B, N)) {
+        mark(0);
+        if (!c_full) DB_TRY(install_full_index(C, M, N));
+        mark(1);
+        DB_TRY(dgemm_tf32_blocks(A, ta, B, tb, C, alpha, use_old ? beta : 0.0, &g_stats.main_flops));
+        mark(2);
+        mark(3);
+        g_stats.c_blocks = C->nblks;
+        return DBCSR_OK;
+    }
     // result pattern: full when both operands are full (and K > 0); else the
     // symbolic product (through stack generation's pattern pass)
     DBuf<double> dA, dB, dC;
@@ -1098,10 +1112,10 @@ extern "C" int dbcsr_multiply(char transa, char transb, double alpha, dbcsr_matr
         return fail(DBCSR_ERR_ARG, "multiply: FP32 runs on the stack path (the dense path offers TF32)");
     g_stats.path = path;
     g_stats.precision = o.precision;
-    // uploads still in flight: the emulated dense path waits for each operand
-    // where it first reads it (the copies of B and C then overlap the work on
-    // A); every other path waits here
-    if (!(path == DBCSR_PATH_DENSE && o.precision == DBCSR_PREC_OZAKI)) {
+    // uploads still in flight: the emulated and TF32 dense paths wait for each
+    // operand where they first read it (the copies of B and C then overlap the
+    // work on A); every other path waits here
+    if (!(path == DBCSR_PATH_DENSE && (o.precision == DBCSR_PREC_OZAKI || o.precision == DBCSR_PREC_TF32))) {
         DB_TRY(await_data(A));
         DB_TRY(await_data(B));
         DB_TRY(await_data(C));

@@ -305,6 +305,22 @@ __device__ __forceinline__ double uni_elem(const UniGeom& G, unsigned bx, unsign
     return G.data[blk * G.X * G.L + in_blk];
 }
 
+// TF32 operand straight from the blocks (fully occupied, one block size per
+// dimension): line x of op(X) rounded to TF32 into out[x * ldk + l], zero for
+// K <= l < ldk
+__global__ void __launch_bounds__(256) k_tf32_uniform(UniGeom G, int64_t ldk, float* __restrict__ out) {
+    const int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (l >= ldk) return;
+    for (int64_t x = blockIdx.y; x < G.nlines; x += gridDim.y) {
+        float v = 0.0f;
+        if (l < G.K) {
+            const unsigned bx = (unsigned)(x / G.X), xw = (unsigned)(x - (int64_t)bx * G.X);
+            v = to_tf32(uni_elem(G, bx, xw, (unsigned)l));
+        }
+        out[x * ldk + l] = v;
+    }
+}
+
 __global__ void __launch_bounds__(256) k_slice_uniform(UniGeom G, const int* __restrict__ ex, int s, int64_t ldk,
                                                        __nv_bfloat16* __restrict__ S) {
     const int lane = threadIdx.x & 31;
@@ -542,6 +558,84 @@ int dgemm_ozaki_blocks(dbcsr_matrix_s* A, bool ta, dbcsr_matrix_s* B, bool tb, d
     DB_TRY(oz_run(M, N, K, ldk, s, SA.p, SB.p, e.p, f.p, alpha, beta, OzOut{C->d_data, 0, base.p, stride.p},
                   main_flops, kernel, C->pending ? C->ready : nullptr));
     C->pending = false;
+    return DBCSR_OK;
+}
+
+static bool uniform_sizes(const std::vector<int>& v) {
+    for (int x : v)
+        if (x != v[0]) return false;
+    return !v.empty();
+}
+
+bool tf32_blocks_ok(const dbcsr_matrix_s* A, const dbcsr_matrix_s* B, int64_t N) {
+    return N >= 256 && tc256_usable() && uniform_sizes(A->h_rs) && uniform_sizes(A->h_cs) &&
+           uniform_sizes(B->h_rs) && uniform_sizes(B->h_cs);
+}
+
+// The TF32 dense product of fully occupied operands without dense copies:
+// the TF32 operands are rounded straight from the blocks, and the 128 x 256
+// tile GEMM writes alpha * acc + beta * C into C's block storage (Sec. III's
+// densification, fused as on the emulated path).
+int dgemm_tf32_blocks(dbcsr_matrix_s* A, bool ta, dbcsr_matrix_s* B, bool tb, dbcsr_matrix_s* C, double alpha,
+                      double beta, double* main_flops) {
+    cudaStream_t st = ctx().stream;
+    const int64_t M = C->h_roff[C->nbr], N = C->h_coff[C->nbc];
+    const int64_t K = ta ? A->h_roff[A->nbr] : A->h_coff[A->nbc];
+    if (M == 0 || N == 0 || K == 0) return fail(DBCSR_ERR_STATE, "tf32 block gemm: empty operand");
+    if (M >= INT32_MAX || N >= INT32_MAX) return fail(DBCSR_ERR_OVERFLOW, "tf32 gemm: dimension too large");
+    const int64_t ldk = cdiv(K, 32) * 32;
+    DBuf<float> AT, BT;
+    DB_TRY(AT.alloc((size_t)M * ldk));
+    DB_TRY(BT.alloc((size_t)N * ldk));
+    auto convert = [&](dbcsr_matrix_s* X, bool x_is_row, int64_t lines, float* out) -> int {
+        DB_TRY(await_data(X));   // an upload still in flight: wait here, after the earlier operand's work
+        const UniGeom G{X->d_data, x_is_row ? X->h_rs[0] : X->h_cs[0], x_is_row ? X->h_cs[0] : X->h_rs[0],
+                        (int64_t)X->nbc, x_is_row ? 1 : 0, lines, K};
+        dim3 g((unsigned)cdiv(ldk, 256), (unsigned)std::min<int64_t>(lines, 65535));
+        k_tf32_uniform<<<g, 256, 0, st>>>(G, ldk, out);
+        DB_KCHECK();
+        return DBCSR_OK;
+    };
+    DB_TRY(convert(A, !ta, M, AT.p));
+    DB_TRY(convert(B, tb, N, BT.p));
+    DBuf<int64_t> base;
+    DBuf<int> stride;
+    DB_TRY(base.alloc(M));
+    DB_TRY(stride.alloc(M));
+    k_full_rows<<<C->nbr, 128, 0, st>>>(C->nbr, C->d_rs, C->d_roff, N, base.p, stride.p);
+    DB_KCHECK();
+    CUtensorMap tmA, tmB;
+    DB_TRY(make_slice_tmap(&tmA, AT.p, ldk, M, 1, 128, 4));
+    DB_TRY(make_slice_tmap(&tmB, BT.p, ldk, N, 1, 256, 4));
+    OzParams p{};
+    p.M = (int)M;
+    p.N = (int)N;
+    p.kblocks = (int)(ldk / 32);
+    p.s = 1;                       // one "level": d = 2, one operand pair
+    p.ksegs = 1;
+    p.kseg_blocks = p.kblocks;
+    p.chunk_blocks = p.kblocks;    // the whole K accumulates in TMEM
+    p.elem_bytes = 4;
+    p.tiles_m = (int)cdiv(M, 128);
+    p.tiles_n = (int)cdiv(N, 128);
+    p.units = (int64_t)p.tiles_m * p.tiles_n;
+    p.C = C->d_data;
+    p.cbase = base.p;
+    p.cstride = stride.p;
+    p.alpha = alpha;
+    p.beta = beta;
+    p.err = ctx().d_flags;
+    p.wait_ns = ctx().wait_ns;
+    DB_TRY(await_data(C));         // the GEMM's epilogue is C's first access
+    DB_CUDA(cudaMemsetAsync(p.err, 0, sizeof(int), st));
+    timer_kernel_begin();
+    DB_TRY(tf32_gemm256_launch(tmA, tmB, p));
+    timer_kernel_end();
+    int h_err = 0;
+    DB_CUDA(cudaMemcpyAsync(&h_err, p.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    DB_CUDA(cudaStreamSynchronize(st));
+    if (h_err) return fail(DBCSR_ERR_TIMEOUT, "tf32 gemm: a tensor-core pipeline wait timed out");
+    if (main_flops) *main_flops = 2.0 * (double)M * (double)N * (double)K;   // algorithmic, unpadded
     return DBCSR_OK;
 }
 

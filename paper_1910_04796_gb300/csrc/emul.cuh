@@ -21,6 +21,13 @@ bool ozaki_blocks_ok(int64_t N);
 int dgemm_ozaki_blocks(dbcsr_matrix_s* A, bool ta, dbcsr_matrix_s* B, bool tb, dbcsr_matrix_s* C, double alpha,
                        double beta, int s, double* main_flops, int kernel);
 
+// TF32 dense product of fully occupied operands with one block size per
+// dimension, written straight into C's block storage (no dense copies);
+// tf32_blocks_ok: whether it applies (N >= 256, the 256-wide kernel usable)
+bool tf32_blocks_ok(const dbcsr_matrix_s* A, const dbcsr_matrix_s* B, int64_t N);
+int dgemm_tf32_blocks(dbcsr_matrix_s* A, bool ta, dbcsr_matrix_s* B, bool tb, dbcsr_matrix_s* C, double alpha,
+                      double beta, double* main_flops);
+
 // TF32 variant of the dense GEMM (tf32.cu).
 int dgemm_tf32(int64_t M, int64_t N, int64_t K, double alpha, const double* A, int64_t lda, const double* B,
                int64_t ldb, double beta, double* C, int64_t ldc, double* main_flops);

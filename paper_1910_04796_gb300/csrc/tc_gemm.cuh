@@ -21,12 +21,23 @@ struct OzParams {
     int64_t ws_stride;    // M * N
     int* ws_i32;          // slices, 256-wide kernel: [s][ksegs][M][ldws] exact int32 level sums (row-major)
     int64_t ldws;         // multiple of 256, >= N
-    double* C;            // tf32: output, column-major
+    double* C;            // tf32: output, column-major (ldc), or by rows (cbase, cstride)
     int64_t ldc;
+    const int64_t* cbase; // tf32, 256-wide kernel: element (i, j) of C at C[cbase[i] + cstride[i] * j]
+    const int* cstride;   //   when cbase is set (C's block storage), else at C[i + j * ldc]
     double alpha, beta;
     int* err;             // set to 1 on a timed-out wait
     uint64_t wait_ns;     // limit of each pipeline wait (ns on the global timer)
 };
+
+// FP64 -> FP32 round-to-nearest-even, then FP32 -> TF32 round-to-nearest
+// with ties away (cvt.rna.tf32.f32)
+__device__ __forceinline__ float to_tf32(double x) {
+    const float f = __double2float_rn(x);
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(f));
+    return __uint_as_float(r);
+}
 
 int make_slice_tmap(CUtensorMap* map, const void* base, int64_t ldk, int64_t rows, int slices, int box_rows,
                     int elem_bytes);

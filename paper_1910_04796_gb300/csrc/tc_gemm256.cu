@@ -217,6 +217,13 @@ __global__ void __launch_bounds__(W_THREADS, 1)
             const int nchunks = (d - 1) * ((kb1 - kb0 + p.chunk_blocks - 1) / p.chunk_blocks);
             const int64_t i = (int64_t)tm * W_TM + row;
             const int64_t j0 = (int64_t)tn * W_TN + half * 128;
+            // TF32: this thread's output row (column-major C, or C's block storage)
+            double* crow = nullptr;
+            int64_t cst = 0;
+            if (MODE == 1 && i < p.M) {
+                crow = p.cbase ? p.C + p.cbase[i] : p.C + i;
+                cst = p.cbase ? (int64_t)p.cstride[i] : p.ldc;
+            }
             int acc[128];
             if (MODE == 0) {
 #pragma unroll
@@ -252,7 +259,7 @@ __global__ void __launch_bounds__(W_THREADS, 1)
                         for (int c = 0; c < 32; c++) {
                             const int64_t j = j0 + g * 32 + c;
                             if (j < p.N) {
-                                double* cp = p.C + i + j * p.ldc;
+                                double* cp = crow + j * cst;
                                 const double x = (double)__uint_as_float(r[c]);
                                 *cp = bu.old ? bu.update(x, *cp) : bu.scale(x);
                             }

@@ -11,12 +11,6 @@ namespace dbcsr {
 
 namespace {
 
-__device__ __forceinline__ float to_tf32(double x) {
-    const float f = __double2float_rn(x);
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(f));
-    return __uint_as_float(r);
-}
 
 // A (column-major M x K) -> AT[i][l] (row-major, ldk), zero for l >= K
 __global__ void __launch_bounds__(256) k_tf32_rows(int64_t M, int64_t K, int64_t ldk, const double* __restrict__ A,

@@ -44,3 +44,31 @@ def test_tf32_transposes_and_ragged():
     Ad, Bd = O.densify(A), O.densify(B)
     e = O.normwise_error(O.densify(got), 2.0 * (O.round_tf32(Ad) @ O.round_tf32(Bd)), Ad, Bd)
     assert e <= 2e-6
+
+
+@pytest.mark.parametrize("ta,tb,beta", [("N", "N", 0.5), ("T", "N", 0.0), ("N", "T", 1.0), ("T", "T", 2.0)])
+def test_tf32_fused_blocks_equal_densified(ta, tb, beta):
+    # fully occupied operands of one block size per dimension (N >= 256): the
+    # TF32 operands come straight from the blocks and the GEMM writes straight
+    # into C's blocks. The same values through the densified path (A without
+    # its first block, which is zero in the fused operand: A no longer fully
+    # occupied) go through the same TF32 rounding and the same GEMM, so the two
+    # results are equal bit for bit.
+    rng = np.random.default_rng(520)
+    Aop = synth.dense_matrix(rng, 12, 10, 22, 32)
+    Bop = synth.dense_matrix(rng, 10, 12, 32, 22)
+    Cm = synth.dense_matrix(rng, 12, 12, 22, 22)
+    m0, n0 = int(Aop.row_sizes[0]), int(Aop.col_sizes[0])
+    data = Aop.data.copy()
+    data[:m0 * n0] = 0.0
+    Az = synth.BlockSparse(Aop.row_sizes, Aop.col_sizes, Aop.blk_row, Aop.blk_col, data)
+    As = synth.BlockSparse(Aop.row_sizes, Aop.col_sizes, Aop.blk_row[1:], Aop.blk_col[1:], data[m0 * n0:])
+    store = lambda M, t: synth.transpose_blocks(M) if t == "T" else M
+    fused, st = gpu_multiply(ta, tb, 1.5, store(Az, ta), store(Bop, tb), beta, Cm, path="dense", precision="tf32")
+    assert st["path"] == dbcsr.PATH_DENSE
+    dense, _ = gpu_multiply(ta, tb, 1.5, store(As, ta), store(Bop, tb), beta, Cm, path="dense", precision="tf32")
+    assert_same_pattern(fused, dense)
+    assert np.array_equal(fused.data, dense.data)
+    Ad, Bd = O.densify(Az), O.densify(Bop)
+    want = 1.5 * (O.round_tf32(Ad) @ O.round_tf32(Bd)) + beta * O.densify(Cm)
+    assert O.normwise_error(O.densify(fused), want, Ad, Bd) <= 2e-6
