@@ -166,7 +166,9 @@ DBCSR_API int dbcsr_init(void *cuda_stream);
 /* Route device allocations through the given hooks (NULL, NULL restores the
  * built-in stream-ordered pool). Every allocation is later returned to the
  * hook (or pool) that made it, so the hooks may be switched at any time; the
- * hook's ctx must stay valid while memory it allocated is alive. */
+ * hook's ctx must stay valid while memory it allocated is alive. (Sec. III:
+ * the GPU execution draws its buffers from memory pools; here the pool can be
+ * the caller's.) */
 DBCSR_API int dbcsr_set_allocator(dbcsr_alloc_fn alloc, dbcsr_free_fn free_fn, void *ctx);
 
 /* Create a matrix (Sec. II: a blocked CSR matrix with per-row and per-column
@@ -210,11 +212,13 @@ DBCSR_API int dbcsr_get_info(dbcsr_matrix m, int *nblkrows, int *nblkcols, int64
 
 /* Block index in storage (CSR) order, to host arrays of length nblks:
  * block row, block column, element offset of the block in the data array.
- * Any output pointer may be NULL. */
+ * Any output pointer may be NULL. (Sec. II: the blocked CSR index of the
+ * stored blocks, each a dense sub-matrix at an offset of the data array.) */
 DBCSR_API int dbcsr_get_index(dbcsr_matrix m, int *blk_row, int *blk_col, int64_t *blk_off);
 
 /* All stored values in storage order (nelems doubles) to `out`, which is host
- * memory if out_on_device == 0 and device memory otherwise. */
+ * memory if out_on_device == 0 and device memory otherwise. (Sec. II: the
+ * blocks' values, each block column-major, concatenated in CSR order.) */
 DBCSR_API int dbcsr_get_data(dbcsr_matrix m, double *out, int out_on_device);
 
 /* Overwrite all stored values (nelems doubles, storage order) from `data`,
@@ -222,12 +226,14 @@ DBCSR_API int dbcsr_get_data(dbcsr_matrix m, double *out, int out_on_device);
  * unchanged, so a kept stack plan (dbcsr_opts.reuse_plan) stays valid. Host
  * values are copied as in dbcsr_create() (from page-locked memory on the
  * transfer stream: `data` must stay unchanged until a call that synchronises
- * has returned); device values are copied before the call returns. */
+ * has returned); device values are copied before the call returns. (Sec. II:
+ * the blocks' values in CSR order, as dbcsr_get_data returns them.) */
 DBCSR_API int dbcsr_set_data(dbcsr_matrix m, const double *data, int data_on_device);
 
 /* Device pointer of the stored values (valid until the next call that changes
  * the matrix) -- for callers that keep data resident on the GPU. A copy of
- * host values still in flight is waited for before the call returns. */
+ * host values still in flight is waited for before the call returns. (Sec. II:
+ * the data array of the blocked CSR format.) */
 DBCSR_API int dbcsr_data_ptr(dbcsr_matrix m, double **dev_ptr);
 
 /* Copy block (row, col) to host `out_colmajor` (row_blk_size x col_blk_size
@@ -253,7 +259,9 @@ DBCSR_API int dbcsr_get_block(dbcsr_matrix m, int row, int col, double *out_colm
 DBCSR_API int dbcsr_multiply(char transa, char transb, double alpha, dbcsr_matrix A, dbcsr_matrix B,
                    double beta, dbcsr_matrix C, const dbcsr_opts *opts);
 
-/* Statistics of the last dbcsr_multiply of this thread. */
+/* Statistics of the last dbcsr_multiply of this thread: block products,
+ * stacks, shapes, the path taken and phase times (Sec. IV-B compares the
+ * blocked and densified runs by their numbers of stacks and their times). */
 DBCSR_API int dbcsr_get_stats(dbcsr_stats *out);
 
 /* Per-shape choice of the FP64 stack kernel (the paper's LIBCUSMM is
@@ -326,13 +334,16 @@ DBCSR_API int dbcsr_dgemm_emulated_noalloc(int64_t M, int64_t N, int64_t K, doub
  * on any thread; not to dbcsr_dgemm_emulated_noalloc (fixed 4 s). */
 DBCSR_API int dbcsr_set_wait_limit(int64_t ns);
 
-/* Wait for all work the library queued on its stream and its transfer stream. */
+/* Wait for all work the library queued on its stream and its transfer stream
+ * (Sec. II: the GPU work and the host-device transfers are ordered on CUDA
+ * streams). */
 DBCSR_API int dbcsr_sync(void);
 
-/* Message of the last error on the calling thread ("" if none). */
+/* Message of the last error on the calling thread ("" if none). The paper has
+ * no counterpart: it is the error channel of this C ABI. */
 DBCSR_API const char *dbcsr_last_error(void);
 
-/* Library version string. */
+/* Library version string. The paper has no counterpart. */
 DBCSR_API const char *dbcsr_version(void);
 
 #ifdef __cplusplus

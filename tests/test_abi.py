@@ -48,3 +48,13 @@ def test_init_without_gpu_fails_loudly():
         assert "no CUDA device" in str(e)
     else:
         raise AssertionError("init() must refuse to run without a GPU")
+
+
+def test_every_entry_point_cites_its_passage():
+    # each declaration of the boundary header is documented with the passage of
+    # the paper that defines the operation, or says the paper has none
+    src = open(os.path.join(ROOT, "include", "dbcsr_gb.h")).read()
+    decls = re.findall(r"(/\*(?:(?!\*/).)*\*/)\s*DBCSR_API[^;]*?(dbcsr_\w+)\s*\(", src, re.S)
+    assert len(decls) >= 20
+    missing = [name for com, name in decls if not re.search(r"Sec\. ?[IVX]+|no counterpart", com)]
+    assert not missing, missing
