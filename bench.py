@@ -201,8 +201,11 @@ def dist_setup(args):
     if world > 1:
         import torch
         import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl" if args.impl != "reference" else "gloo")
+        if args.impl == "reference":     # the oracle runs on the host cores: no GPU
+            dist.init_process_group("gloo")
+        else:
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl")
     return world, rank, local
 
 

@@ -7,7 +7,9 @@
   throttle reasons seen);
 * the roofline denominators: MEASURED_PEAKS.json, else the stated fallback;
 * the reference arm (the oracle on the host cores) works and prints on rank 0
-  only, with the warm-up steps it reports.
+  only, with the warm-up steps it reports;
+* on two gloo ranks: the set-up, the maximum of the ranks' timings that every
+  rank sees, and the reference arm's single line from rank 0.
 """
 import hashlib
 import os
@@ -137,3 +139,44 @@ def test_reference_arm_runs_on_rank_zero_only(capsys):
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["warmup"] == 3
     assert line["cpu_baseline"]["kind"] == "oracle" and line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
+
+
+def _rank_worker(rank, world, port, out_dir):
+    import argparse
+    import contextlib
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    args = argparse.Namespace(impl="reference", workload="small-sparse", scale=1.0, occ=0.1, steps=1,
+                              warmup=3, ref_rows=2)
+    w, r, _ = bench.dist_setup(args)
+    # each rank's timing differs; every rank must see the slowest one
+    slowest = bench.max_over_ranks(1.5 + r, w)
+    bench.barrier(w)
+    with open(os.path.join(out_dir, f"out{rank}.txt"), "w") as f, contextlib.redirect_stdout(f):
+        rc = bench.run_reference(args, w, r)
+    with open(os.path.join(out_dir, f"max{rank}.txt"), "w") as f:
+        f.write(f"{w} {r} {slowest} {rc}")
+
+
+def test_two_gloo_ranks_reduce_max_and_print_once(tmp_path):
+    import multiprocessing as mp
+    import socket
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    ctx = mp.get_context("spawn")
+    procs = [ctx.Process(target=_rank_worker, args=(r, 2, port, str(tmp_path))) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    for r in range(2):
+        w, rr, slowest, rc = (tmp_path / f"max{r}.txt").read_text().split()
+        assert (int(w), int(rr), float(slowest), int(rc)) == (2, r, 2.5, 0)
+    import json
+    assert (tmp_path / "out1.txt").read_text() == ""          # rank 1: no work, no line
+    lines = (tmp_path / "out0.txt").read_text().strip().splitlines()
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
